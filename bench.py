@@ -1,0 +1,296 @@
+"""Benchmark of the fused MPDATA step on the 1024x512x64 rotation-blob grid.
+
+One bench step = one user solve: 50 MPDATA time steps of the full grid
+(periodic x/y, rigid lids in z, solid-body rotation max |C| = 0.5, h = 1 +
+0.1 sin, 8 Gaussian blobs), i.e. 50 launches of the fused kernel.  The metric
+is Gcell-steps/s = nx*ny*nz*50 / (time per solve).
+
+Prints ONE JSON line (rank 0):
+  value      device time (CUDA events on the launch stream), inputs resident
+  e2e        the same metric through mpdata_solve_host from pinned host
+             memory (copies of the 5 inputs in and psi out inside the region)
+  roofline   the fused kernel against the measured HBM copy peak under the
+             6-field model (24 B per cell-step in FP32)
+  cpu_baseline  the FP64 oracle on a bounded sample of the same workload
+  clocks     nvidia-smi samples taken during the timed region
+
+--impl reference times the oracle itself (the CPU reference of this build)
+on a bounded sample per step.  Under torchrun (N > 1) every rank runs its own
+replica of the problem (the workload does not shard across GPUs here).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MPDATA Gcell-steps/s and % HBM roofline; served p50/p99 latency vs plain"
+UNIT = "Gcell-steps/s"
+NX, NY, NZ, NSTEPS = 1024, 512, 64, 50
+FIELDS = 6  # read psi, h, u1, u2, u3; write psi
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--path", default="fused", choices=["fused", "stages"])
+    ap.add_argument("--tile", default=None, help="fused tile, e.g. 32x16")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-clocks", action="store_true")
+    return ap.parse_args()
+
+
+def dist_init(args):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if args.impl == "native" else "gloo"
+        dist.init_process_group(backend)
+        pg = dist
+    return rank, world, local, pg
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def kernel_traffic(ncells):
+    """DRAM bytes per launch of the fused kernel from the committed ncu
+    summary, valid only while the kernel source is unchanged."""
+    path = os.path.join(ROOT, "profiles", "fused_traffic.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f)
+        src = open(os.path.join(ROOT, "paper_1507_01265_gb300", "csrc", "mpdata_fused.cu"), "rb").read()
+        if rec.get("source_sha256") != hashlib.sha256(src).hexdigest():
+            return None
+        return float(rec["bytes_per_cell"]) * ncells
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi samples during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index, enabled=True):
+        self.index = index
+        self.proc = None
+        self.enabled = enabled
+
+    def __enter__(self):
+        if self.enabled:
+            try:
+                self.proc = subprocess.Popen(
+                    ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                     "--format=csv,noheader,nounits", "-lms", "100"],
+                    stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            except Exception:
+                self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.out = ""
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        for line in (self.out or "").strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+            except ValueError:
+                continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, r in rows for i, v in enumerate(r) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+def oracle_sample(seconds_hint=15.0):
+    """Time the FP64 oracle, as it stands, on a bounded sample of the
+    workload: the first `rows` y-rows of the 1024x512x64 grid for one step
+    (one host core)."""
+    import numpy as np
+    import gen.fields as F
+    import oracle
+    rows = 64 if seconds_hint >= 10 else 16
+    f = F.rotation_blobs()
+    sub = lambda a: np.ascontiguousarray(a[:, :rows, :], dtype=np.float64)
+    h, psi, u1, u2, u3 = (sub(a) for a in (f.h, f.psi, f.u1, f.u2, f.u3))
+    cfg = oracle.Config(f.nx, rows, f.nz, (1, 1, 0))
+    oracle.load()
+    t0 = time.perf_counter()
+    oracle.run(cfg, h, psi, u1, u2, u3, nsteps=1)
+    dt = time.perf_counter() - t0
+    cells = f.nx * rows * f.nz
+    return {"value": cells / dt / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "1 step of a %dx%dx%d slab (first %d y-rows) of the 1024x512x64 workload, "
+                      "serial FP64 C, %.1f s" % (f.nx, rows, f.nz, rows, dt)}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    import gen.fields as F  # noqa: F401
+    times = []
+    info = None
+    for i in range(args.warmup + args.steps):
+        r = oracle_sample(seconds_hint=2.0)
+        if i >= args.warmup:
+            times.append(r["value"])
+        info = r
+    v = statistics.mean(times)
+    line = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": "rotation_blobs 1024x512x64 (sampled slab)", "grid": [NX, NY, NZ]},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": info["sample"]},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    args = parse()
+    rank, world, local, dist = dist_init(args)
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import numpy as np
+    import torch
+
+    import gen.fields as F
+    import paper_1507_01265_gb300 as mp
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    f = F.rotation_blobs(nx=NX, ny=NY, nz=NZ, nsteps=NSTEPS)
+    ncells = f.ncells
+    tile = tuple(int(v) for v in args.tile.split("x")) if args.tile else None
+    solver = mp.Solver(f.nx, f.ny, f.nz, periodic=f.periodic, path=args.path, tile=tile)
+    t = [torch.from_numpy(a).to(dev) for a in (f.h, f.psi, f.u1, f.u2, f.u3)]
+    h, psi, u1, u2, u3 = t
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        solver.step(h, psi, u1, u2, u3, NSTEPS, stream)
+    barrier()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local, enabled=not args.no_clocks) as clk:
+        barrier()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            solver.step(h, psi, u1, u2, u3, NSTEPS, stream)
+        ev1.record(stream)
+        barrier()
+    ms = ev0.elapsed_time(ev1)
+    if dist is not None:
+        tt = torch.tensor([ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    ms_per_step = ms / args.steps
+    launches = args.steps * NSTEPS
+    value = world * ncells * NSTEPS * args.steps / (ms * 1e-3) / 1e9
+
+    # roofline of the fused kernel: the timed region holds only its launches
+    peak, peak_kind = measured_peaks()
+    algo_bytes = FIELDS * 4 * ncells
+    launch_s = ms * 1e-3 / launches
+    achieved = algo_bytes / launch_s / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": kernel_traffic(ncells),
+                "peak_kind": peak_kind, "kernel": "k_fused" if args.path == "fused" else "stage kernels",
+                "algorithmic_bytes_per_launch": algo_bytes}
+
+    # end to end through the public host API
+    e2e = None
+    if not args.no_e2e:
+        pin = lambda a: torch.from_numpy(a).pin_memory()
+        hh, hp, h1, h2, h3 = (pin(a) for a in (f.h, f.psi, f.u1, f.u2, f.u3))
+        solver.solve_host(hh, hp.clone(), h1, h2, h3, NSTEPS, stream)  # allocate device copies
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            solver.solve_host(hh, hp, h1, h2, h3, NSTEPS, stream)
+        dt = time.perf_counter() - t0
+        if dist is not None:
+            tt = torch.tensor([dt], device=dev)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            dt = float(tt.item())
+        e2e = {"value": world * ncells * NSTEPS * args.e2e_steps / dt / 1e9, "unit": UNIT,
+               "h2d_bytes_per_step": 5 * 4 * ncells, "d2h_bytes_per_step": 4 * ncells,
+               "steps": args.e2e_steps}
+
+    if rank == 0:
+        cpu = None if args.no_cpu_baseline else oracle_sample()
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "rotation_blobs 1024x512x64, periodic x/y, lid z, "
+                                   "50 MPDATA steps per solve",
+                       "grid": [NX, NY, NZ], "mpdata_steps_per_step": NSTEPS,
+                       "path": args.path, "tile": list(solver_tile(args, tile)),
+                       "iterations": 2, "nonoscillatory": True,
+                       "l2": "inputs 671 MB + output 134 MB per launch > 129 MB L2 (no flush)",
+                       "parallelism": "replicas" if world > 1 else "single"},
+            "roofline": roofline, "e2e": e2e, "cpu_baseline": cpu,
+            "clocks": clk.summary(), "gpu_launches": launches,
+            "pct_hbm_roofline": 100.0 * roofline["frac"],
+        }
+        print(json.dumps(line), flush=True)
+    solver.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def solver_tile(args, tile):
+    if args.path != "fused":
+        return ()
+    return tile or (32, 16)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

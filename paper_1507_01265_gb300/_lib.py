@@ -1,0 +1,93 @@
+"""ctypes binding of libmpdata (include/mpdata.h).
+
+Argument marshalling only: every step of the advection scheme runs in the
+CUDA kernels of libmpdata.so.  There is no CPU fallback -- if the library is
+missing, importing this module raises.  PyTorch is used for device memory
+and streams (tensors are passed by data pointer, streams by handle).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libmpdata.so")
+
+MPDATA_OK = 0
+MPDATA_EINVAL = -1
+MPDATA_ENOMEM = -2
+MPDATA_ECUDA = -3
+MPDATA_EBUSY = -4
+MPDATA_ETIMEDOUT = -5
+MPDATA_ENOENT = -6
+MPDATA_ECANCELED = -7
+
+MPDATA_F32 = 0
+MPDATA_F64 = 1
+MPDATA_PATH_FUSED = 0
+MPDATA_PATH_STAGES = 1
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("size", ctypes.c_uint32), ("iterations", ctypes.c_int32),
+                ("nonoscillatory", ctypes.c_int32), ("periodic", ctypes.c_int32 * 3),
+                ("dtype", ctypes.c_int32), ("path", ctypes.c_int32),
+                ("tile_x", ctypes.c_int32), ("tile_y", ctypes.c_int32), ("eps", ctypes.c_double)]
+
+
+class MpdataError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        self.code = code
+        super().__init__("%s: %s (%d): %s" % (what, strerror(code), code, last_error_message()))
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError("libmpdata.so is not built (%s); run "
+                          "`python -c 'import __graft_entry__ as g; g.build()'`" % LIB_PATH)
+    lib = ctypes.CDLL(LIB_PATH)
+    P, I, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    H = ctypes.c_void_p  # mpdata_t*
+    sig = {
+        "mpdata_opts_default": (None, [ctypes.POINTER(Opts)]),
+        "mpdata_create": (I, [I, I, I, ctypes.POINTER(Opts), ctypes.POINTER(H)]),
+        "mpdata_destroy": (I, [H]),
+        "mpdata_step": (I, [H, P, P, P, P, P, I, P]),
+        "mpdata_solve_host": (I, [H, P, P, P, P, P, I, P]),
+        "mpdata_mass": (I, [H, P, P, P, P]),
+        "mpdata_strerror": (ctypes.c_char_p, [I]),
+        "mpdata_last_error_message": (ctypes.c_char_p, []),
+        "mpdata_version": (ctypes.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _ = D
+    return lib
+
+
+lib = _load()
+
+
+def strerror(code: int) -> str:
+    return lib.mpdata_strerror(code).decode()
+
+
+def last_error_message() -> str:
+    return lib.mpdata_last_error_message().decode()
+
+
+def version() -> str:
+    return lib.mpdata_version().decode()
+
+
+def check(code: int, what: str) -> None:
+    if code != MPDATA_OK:
+        raise MpdataError(code, what)
+
+
+def default_opts() -> Opts:
+    o = Opts()
+    lib.mpdata_opts_default(ctypes.byref(o))
+    return o

@@ -1,0 +1,240 @@
+// C ABI of libmpdata (declared in include/mpdata.h): argument checking,
+// device-buffer ownership and the step loop.  All arithmetic of the step runs
+// in the kernels of mpdata_fused.cu / mpdata_stages.cu / mpdata_reduce.cu.
+#include <stdarg.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+#include <string>
+
+#include "mpdata_internal.cuh"
+
+using mpdata::Grid;
+
+struct mpdata_handle {
+    int nx, ny, nz;
+    long long n;
+    size_t esize;
+    mpdata_opts opts;
+    Grid grid;
+    int tile_x, tile_y;
+    void *scratch;            // psi-sized ping-pong partner
+    mpdata::StageBuffers st;  // stage-per-kernel intermediates (path STAGES only)
+    double *partials;         // mass reduction partials (kReduceBlocks x 3)
+    void *host_fields[5];     // device copies for mpdata_solve_host (lazy)
+};
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const char *fmt, ...) __attribute__((format(printf, 2, 3)));
+int fail(int code, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char *what) {
+    return fail(MPDATA_ECUDA, "%s: %s (%s)", what, cudaGetErrorName(e), cudaGetErrorString(e));
+}
+
+bool aligned16(const void *p) { return p && ((uintptr_t)p & 15u) == 0; }
+
+int check_opts(const mpdata_opts *o) {
+    if (o->size < sizeof(mpdata_opts)) return fail(MPDATA_EINVAL, "opts.size too small (use mpdata_opts_default)");
+    if (o->iterations != 1 && o->iterations != 2) return fail(MPDATA_EINVAL, "iterations must be 1 or 2");
+    if (o->nonoscillatory != 0 && o->nonoscillatory != 1) return fail(MPDATA_EINVAL, "nonoscillatory must be 0 or 1");
+    for (int d = 0; d < 3; ++d)
+        if (o->periodic[d] != 0 && o->periodic[d] != 1) return fail(MPDATA_EINVAL, "periodic[%d] must be 0 or 1", d);
+    if (o->dtype != MPDATA_F32 && o->dtype != MPDATA_F64) return fail(MPDATA_EINVAL, "dtype must be MPDATA_F32 or MPDATA_F64");
+    if (o->path != MPDATA_PATH_FUSED && o->path != MPDATA_PATH_STAGES) return fail(MPDATA_EINVAL, "unknown path");
+    if (!(o->eps > 0.0)) return fail(MPDATA_EINVAL, "eps must be > 0");
+    return MPDATA_OK;
+}
+
+void free_handle(mpdata_t *m) {
+    if (!m) return;
+    cudaFree(m->scratch);
+    cudaFree(m->st.psi1);
+    cudaFree(m->st.v1);
+    cudaFree(m->st.v2);
+    cudaFree(m->st.v3);
+    cudaFree(m->st.bup);
+    cudaFree(m->st.bdn);
+    cudaFree(m->partials);
+    for (int f = 0; f < 5; ++f) cudaFree(m->host_fields[f]);
+    delete m;
+}
+
+int launch_one(mpdata_t *m, const void *h, const void *src, const void *u1, const void *u2,
+               const void *u3, void *dst, cudaStream_t s) {
+    const mpdata_opts &o = m->opts;
+    cudaError_t e;
+    if (o.iterations == 1)
+        e = mpdata::launch_donor(o.dtype, m->grid, h, src, u1, u2, u3, dst, s);
+    else if (o.path == MPDATA_PATH_STAGES)
+        e = mpdata::launch_stage_step(o.dtype, m->grid, o.iterations, o.nonoscillatory, o.eps, h,
+                                      src, u1, u2, u3, dst, m->st, s);
+    else
+        e = mpdata::launch_fused_step(o.dtype, m->grid, o.nonoscillatory, o.eps, m->tile_x,
+                                      m->tile_y, h, src, u1, u2, u3, dst, s);
+    return e == cudaSuccess ? MPDATA_OK : cuda_fail(e, "kernel launch");
+}
+
+}  // namespace
+
+extern "C" {
+
+void mpdata_opts_default(mpdata_opts *o) {
+    if (!o) return;
+    memset(o, 0, sizeof *o);
+    o->size = sizeof *o;
+    o->iterations = 2;
+    o->nonoscillatory = 1;
+    o->periodic[0] = o->periodic[1] = o->periodic[2] = 1;
+    o->dtype = MPDATA_F32;
+    o->path = MPDATA_PATH_FUSED;
+    o->tile_x = o->tile_y = 0;
+    o->eps = 1e-15;
+}
+
+int mpdata_create(int nx, int ny, int nz, const mpdata_opts *opts, mpdata_t **out) {
+    if (!out) return fail(MPDATA_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (nx < 1 || ny < 1 || nz < 1) return fail(MPDATA_EINVAL, "dims must be >= 1 (got %d x %d x %d)", nx, ny, nz);
+    long long n = (long long)nx * ny * nz;
+    if (n >= (1LL << 31)) return fail(MPDATA_EINVAL, "grid of %lld cells is too large (limit 2^31 - 1)", n);
+    if (ny > 65535 || nz > 65535) return fail(MPDATA_EINVAL, "ny and nz must be <= 65535");
+    mpdata_opts o;
+    if (opts) o = *opts; else mpdata_opts_default(&o);
+    int rc = check_opts(&o);
+    if (rc) return rc;
+    int tx = o.tile_x, ty = o.tile_y;
+    if (tx == 0 && ty == 0) mpdata::fused_default_tile(o.dtype, &tx, &ty);
+    if (o.path == MPDATA_PATH_FUSED && o.iterations == 2 && !mpdata::fused_tile_supported(o.dtype, tx, ty))
+        return fail(MPDATA_EINVAL, "no fused kernel for tile %d x %d", tx, ty);
+
+    mpdata_t *m = new (std::nothrow) mpdata_handle();
+    if (!m) return fail(MPDATA_ENOMEM, "host allocation failed");
+    memset(m, 0, sizeof *m);
+    m->nx = nx; m->ny = ny; m->nz = nz; m->n = n;
+    m->opts = o;
+    m->esize = o.dtype == MPDATA_F64 ? sizeof(double) : sizeof(float);
+    m->grid.nx = nx; m->grid.ny = ny; m->grid.nz = nz;
+    for (int d = 0; d < 3; ++d) m->grid.per[d] = o.periodic[d];
+    m->tile_x = tx; m->tile_y = ty;
+    const size_t bytes = (size_t)n * m->esize;
+    cudaError_t e = cudaMalloc(&m->scratch, bytes);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&m->partials, sizeof(double) * 3 * mpdata::kReduceBlocks);
+    if (e == cudaSuccess && o.path == MPDATA_PATH_STAGES) {
+        void **b[6] = {&m->st.psi1, &m->st.v1, &m->st.v2, &m->st.v3, &m->st.bup, &m->st.bdn};
+        for (int i = 0; i < 6 && e == cudaSuccess; ++i) e = cudaMalloc(b[i], bytes);
+    }
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        free_handle(m);
+        return e == cudaErrorMemoryAllocation ? fail(MPDATA_ENOMEM, "device allocation of %zu bytes failed", bytes)
+                                              : cuda_fail(e, "cudaMalloc");
+    }
+    *out = m;
+    return MPDATA_OK;
+}
+
+int mpdata_destroy(mpdata_t *m) {
+    free_handle(m);
+    return MPDATA_OK;
+}
+
+int mpdata_step(mpdata_t *m, const void *h, void *psi, const void *u1, const void *u2,
+                const void *u3, int nsteps, void *stream) {
+    if (!m) return fail(MPDATA_EINVAL, "handle is NULL");
+    if (nsteps < 0) return fail(MPDATA_EINVAL, "nsteps must be >= 0");
+    const void *ptrs[5] = {h, psi, u1, u2, u3};
+    const char *names[5] = {"h", "psi", "u1", "u2", "u3"};
+    for (int f = 0; f < 5; ++f)
+        if (!aligned16(ptrs[f])) return fail(MPDATA_EINVAL, "%s is NULL or not 16-byte aligned", names[f]);
+    if (psi == m->scratch) return fail(MPDATA_EINVAL, "psi aliases the handle's scratch buffer");
+    if (nsteps == 0) return MPDATA_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    void *cur = psi, *other = m->scratch;
+    if (nsteps & 1) {
+        cudaError_t e = cudaMemcpyAsync(m->scratch, psi, (size_t)m->n * m->esize, cudaMemcpyDeviceToDevice, s);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync");
+        cur = m->scratch;
+        other = psi;
+    }
+    for (int st = 0; st < nsteps; ++st) {
+        int rc = launch_one(m, h, cur, u1, u2, u3, other, s);
+        if (rc) return rc;
+        void *tmp = cur; cur = other; other = tmp;
+    }
+    return MPDATA_OK;
+}
+
+int mpdata_solve_host(mpdata_t *m, const void *h, void *psi, const void *u1, const void *u2,
+                      const void *u3, int nsteps, void *stream) {
+    if (!m) return fail(MPDATA_EINVAL, "handle is NULL");
+    const void *src[5] = {h, psi, u1, u2, u3};
+    const char *names[5] = {"h", "psi", "u1", "u2", "u3"};
+    for (int f = 0; f < 5; ++f)
+        if (!src[f]) return fail(MPDATA_EINVAL, "%s is NULL", names[f]);
+    if (nsteps < 0) return fail(MPDATA_EINVAL, "nsteps must be >= 0");
+    const size_t bytes = (size_t)m->n * m->esize;
+    cudaStream_t s = (cudaStream_t)stream;
+    for (int f = 0; f < 5; ++f) {
+        if (!m->host_fields[f]) {
+            cudaError_t e = cudaMalloc(&m->host_fields[f], bytes);
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                m->host_fields[f] = nullptr;
+                return fail(MPDATA_ENOMEM, "device allocation of %zu bytes failed", bytes);
+            }
+        }
+        cudaError_t e = cudaMemcpyAsync(m->host_fields[f], src[f], bytes, cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync host to device");
+    }
+    int rc = mpdata_step(m, m->host_fields[0], m->host_fields[1], m->host_fields[2],
+                         m->host_fields[3], m->host_fields[4], nsteps, stream);
+    if (rc) return rc;
+    cudaError_t e = cudaMemcpyAsync(psi, m->host_fields[1], bytes, cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync device to host");
+    e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    return MPDATA_OK;
+}
+
+int mpdata_mass(mpdata_t *m, const void *h, const void *psi, void *out3, void *stream) {
+    if (!m) return fail(MPDATA_EINVAL, "handle is NULL");
+    if (!aligned16(h) || !aligned16(psi)) return fail(MPDATA_EINVAL, "h or psi is NULL or not 16-byte aligned");
+    if (!out3 || ((uintptr_t)out3 & 7u)) return fail(MPDATA_EINVAL, "out3 is NULL or not 8-byte aligned");
+    cudaError_t e = mpdata::launch_mass(m->opts.dtype, m->n, h, psi, m->partials, (double *)out3,
+                                        (cudaStream_t)stream);
+    return e == cudaSuccess ? MPDATA_OK : cuda_fail(e, "mass kernel launch");
+}
+
+const char *mpdata_strerror(int code) {
+    switch (code) {
+    case MPDATA_OK: return "ok";
+    case MPDATA_EINVAL: return "invalid argument";
+    case MPDATA_ENOMEM: return "out of memory";
+    case MPDATA_ECUDA: return "CUDA error";
+    case MPDATA_EBUSY: return "busy: over budget";
+    case MPDATA_ETIMEDOUT: return "timed out";
+    case MPDATA_ENOENT: return "no such ticket";
+    case MPDATA_ECANCELED: return "cancelled";
+    default: return "unknown error";
+    }
+}
+
+const char *mpdata_last_error_message(void) { return g_last_error.c_str(); }
+
+const char *mpdata_version(void) { return "mpdata-gb300 0.1 (sm_103a)"; }
+
+}  // extern "C"

@@ -1,0 +1,57 @@
+// Internal declarations shared by the CUDA translation units of libmpdata.
+// (Nothing here is part of the public ABI; see include/mpdata.h.)
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "mpdata.h"
+
+namespace mpdata {
+
+// Grid description passed by value to every kernel.
+struct Grid {
+    int nx, ny, nz;
+    int per[3];  // 1 periodic, 0 rigid lid
+};
+
+// Map a cell index that is at most one grid length outside [0, n) into
+// range: wrap on a periodic axis, clamp (zero-gradient ghost) on a lid axis.
+__device__ __forceinline__ int cell_index(int a, int n, int per) {
+    if (a >= 0 && a < n) return a;
+    if (per) return a < 0 ? a + n : a - n;
+    return a < 0 ? 0 : n - 1;
+}
+
+// Upstream flux through a face with velocity U between left value L and
+// right value R: [U]+ L + [U]- R (a select; identical to the max/min form
+// for finite values).
+template <typename T>
+__device__ __forceinline__ T upstream_flux(T U, T L, T R) {
+    return U > T(0) ? U * L : U * R;
+}
+
+// Launchers of the stage-per-kernel path (mpdata_stages.cu).
+struct StageBuffers {
+    void *psi1, *v1, *v2, *v3, *bup, *bdn;
+};
+cudaError_t launch_donor(int dtype, const Grid &g, const void *h, const void *psi, const void *w1,
+                         const void *w2, const void *w3, void *out, cudaStream_t s);
+cudaError_t launch_stage_step(int dtype, const Grid &g, int iterations, int nonosc, double eps,
+                              const void *h, const void *psi, const void *u1, const void *u2,
+                              const void *u3, void *out, const StageBuffers &b, cudaStream_t s);
+
+// Fused step (mpdata_fused.cu).  Returns cudaErrorInvalidValue for a tile
+// shape that has no compiled instance.
+cudaError_t launch_fused_step(int dtype, const Grid &g, int nonosc, double eps, int tile_x,
+                              int tile_y, const void *h, const void *psi, const void *u1,
+                              const void *u2, const void *u3, void *out, cudaStream_t s);
+bool fused_tile_supported(int dtype, int tile_x, int tile_y);
+void fused_default_tile(int dtype, int *tile_x, int *tile_y);
+
+// Deterministic FP64 diagnostics (mpdata_reduce.cu).
+constexpr int kReduceBlocks = 1024;  // fixed, so the summation tree never changes
+cudaError_t launch_mass(int dtype, long long n, const void *h, const void *psi, double *partials,
+                        double *out3, cudaStream_t s);
+
+}  // namespace mpdata

@@ -1,0 +1,198 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerances: FP32 state, max|dpsi| <= 1e-5 max|psi| after 10 steps and
+<= 1e-4 max|psi| after 100 steps; FP64 GPU path <= 1e-12 relative.  Exact
+cases (shift at Courant 1, constant fields) are compared bit for bit."""
+import numpy as np
+import pytest
+
+import gen.fields as F
+from gpu_helpers import oracle_at, rand_problem, rel_err, run_gpu, run_oracle
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import __graft_entry__ as g
+    g.build()
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+
+
+# ---- the 64x32x16 parity configuration --------------------------------------------------
+
+@pytest.mark.parametrize("path", ["fused", "stages"])
+def test_gaussian_constant_f32_10_steps(path):
+    f = F.gaussian_constant()
+    got = run_gpu(f, 10, path=path)
+    want = run_oracle(f, 10)
+    assert rel_err(got, want) <= 1e-5
+
+
+@pytest.mark.parametrize("path", ["fused", "stages"])
+def test_gaussian_constant_f32_100_steps(path):
+    f = F.gaussian_constant()
+    got = run_gpu(f, 100, path=path)
+    want = run_oracle(f, 100)
+    assert rel_err(got, want) <= 1e-4
+
+
+@pytest.mark.parametrize("path", ["fused", "stages"])
+def test_gaussian_constant_f64(path):
+    f = F.gaussian_constant()
+    got = run_gpu(f, 10, dtype="f64", path=path)
+    want = run_oracle(f, 10)
+    assert rel_err(got, want) <= 1e-12
+
+
+# ---- edge shapes: ragged tiles, tiny grids, lids on every axis --------------------------
+
+EDGE = [
+    (37, 23, 11, (1, 1, 1)), (5, 3, 2, (1, 1, 1)), (1, 1, 1, (1, 1, 1)), (1, 1, 1, (0, 0, 0)),
+    (9, 40, 7, (0, 1, 0)), (70, 5, 3, (1, 0, 0)), (33, 17, 20, (1, 1, 0)), (64, 32, 16, (0, 0, 0)),
+    (32, 16, 4, (1, 1, 1)), (31, 15, 6, (0, 1, 1)), (65, 33, 3, (1, 0, 1)), (2, 70, 2, (0, 0, 1)),
+]
+
+
+@pytest.mark.parametrize("nx,ny,nz,per", EDGE)
+@pytest.mark.parametrize("nonosc", [True, False])
+def test_edge_shapes_f64(nx, ny, nz, per, nonosc):
+    f = rand_problem((nz, ny, nx), seed=nx * 131 + ny * 7 + nz, periodic=per)
+    want = run_oracle(f, 3, nonosc=nonosc)
+    for path in ("fused", "stages"):
+        got = run_gpu(f, 3, dtype="f64", path=path, nonosc=nonosc)
+        assert rel_err(got, want) <= 1e-12, path
+
+
+@pytest.mark.parametrize("nx,ny,nz,per", EDGE)
+@pytest.mark.parametrize("tile", [None, (24, 24), (16, 16)])
+def test_edge_shapes_f32(nx, ny, nz, per, tile):
+    f = rand_problem((nz, ny, nx), seed=nx * 17 + ny * 5 + nz, periodic=per)
+    want = run_oracle(f, 3)
+    got = run_gpu(f, 3, tile=tile)
+    assert rel_err(got, want) <= 1e-5
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+def test_donor_only(dtype):
+    f = rand_problem((9, 14, 33), seed=3, periodic=(1, 0, 1))
+    got = run_gpu(f, 4, dtype=dtype, iterations=1)
+    want = run_oracle(f, 4, iterations=1)
+    assert rel_err(got, want) <= (1e-5 if dtype == "f32" else 1e-12)
+
+
+# ---- exact cases ------------------------------------------------------------------------
+
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+@pytest.mark.parametrize("path", ["fused", "stages"])
+def test_shift_at_courant_one_is_exact(dtype, path):
+    shape = (6, 20, 37)
+    r = np.random.default_rng(11)
+    psi = r.integers(1, 2 ** 20, size=shape).astype(np.float32)
+    for axis in range(3):
+        for sign in (1.0, -1.0):
+            u = [np.zeros(shape, np.float32) for _ in range(3)]
+            u[axis][:] = sign
+            f = F.Fields("shift", shape[2], shape[1], shape[0], (1, 1, 1),
+                         np.ones(shape, np.float32), psi, u[0], u[1], u[2], 3, 0)
+            got = run_gpu(f, 3, dtype=dtype, path=path)
+            assert np.array_equal(got, np.roll(psi.astype(np.float64), int(sign) * 3, axis=2 - axis))
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+def test_constant_is_preserved_exactly(dtype):
+    nx, ny, nz = 70, 41, 9
+    u1, u2, u3 = F.rotation_courant(nx, ny, nz, 0.5)
+    h = F.sine_density(nx, ny, nz)
+    psi = np.full((nz, ny, nx), 3.25, np.float32)
+    f = F.Fields("const", nx, ny, nz, (1, 1, 0), h, psi, u1, u2, u3, 5, 0)
+    got = run_gpu(f, 5, dtype=dtype)
+    assert np.all(got == 3.25)
+
+
+# ---- conservation and diagnostics -------------------------------------------------------
+
+def test_mass_conservation_and_diagnostics():
+    import torch
+    import oracle
+    import paper_1507_01265_gb300 as mp
+    f = rand_problem((12, 30, 45), seed=5, periodic=(1, 1, 0))
+    dev = torch.device("cuda")
+    for dtype, tol in (("f64", 1e-12), ("f32", 1e-5)):
+        td = torch.float64 if dtype == "f64" else torch.float32
+        t = [torch.from_numpy(a).to(dev, td) for a in (f.h, f.psi, f.u1, f.u2, f.u3)]
+        with mp.Solver(f.nx, f.ny, f.nz, periodic=f.periodic, dtype=dtype) as s:
+            m0 = s.mass(t[0], t[1]).cpu().numpy()
+            ref = oracle.mass(t[0].double().cpu().numpy(), t[1].double().cpu().numpy())
+            assert abs(m0[0] / ref - 1) <= 1e-14
+            assert m0[1] == t[1].min().item() and m0[2] == t[1].max().item()
+            s.step(*t, 10)
+            m1 = s.mass(t[0], t[1]).cpu().numpy()
+            assert abs(m1[0] / m0[0] - 1) <= tol, dtype
+            again = s.mass(t[0], t[1]).cpu().numpy()
+            assert np.array_equal(m1, again)  # bit-reproducible
+
+
+def test_solve_host_and_odd_steps_match_step():
+    import torch
+    import paper_1507_01265_gb300 as mp
+    f = rand_problem((8, 19, 27), seed=9)
+    a = run_gpu(f, 5)
+    b = run_gpu(f, 2)
+    b = run_gpu(f, 3, psi=b.astype(np.float32))
+    assert np.array_equal(a, b)
+    psi = f.psi.copy()
+    with mp.Solver(f.nx, f.ny, f.nz) as s:
+        s.solve_host(f.h, psi, f.u1, f.u2, f.u3, 5)
+        s.solve_host(f.h, psi, f.u1, f.u2, f.u3, 0)
+    assert np.array_equal(psi.astype(np.float64), a)
+    torch.cuda.synchronize()
+
+
+def test_fused_matches_stage_per_kernel():
+    f = F.rotation_blobs(nx=96, ny=64, nz=24, nsteps=6)
+    a = run_gpu(f, 6, path="fused")
+    b = run_gpu(f, 6, path="stages")
+    assert rel_err(a, b) <= 1e-6
+
+
+def test_bad_pointers_are_rejected():
+    import torch
+    import paper_1507_01265_gb300 as mp
+    with mp.Solver(8, 8, 8) as s:
+        t = torch.zeros(8 * 8 * 8 + 1, device="cuda")
+        view = t[1:]  # 4-byte offset: not 16-byte aligned
+        with pytest.raises(mp.MpdataError) as e:
+            s.step(view, view, view, view, view, 1)
+        assert e.value.code == -1
+
+
+# ---- the 1024x512x64 roofline configuration, in the launch configuration bench.py times ---
+
+@pytest.mark.parametrize("nsteps", [1, 2])
+def test_rotation_blobs_full_size_sampled(nsteps):
+    f = F.rotation_blobs()  # 1024 x 512 x 64, periodic x/y, lids in z
+    got = run_gpu(f, nsteps)
+    r = np.random.default_rng(100 + nsteps)
+    samples = [(int(r.integers(f.nz)), int(r.integers(f.ny)), int(r.integers(f.nx)))
+               for _ in range(120)]
+    samples += [(0, 0, 0), (f.nz - 1, f.ny - 1, f.nx - 1), (0, f.ny - 1, 5), (f.nz - 1, 3, f.nx - 1)]
+    want = oracle_at(f, samples, nsteps)
+    vals = np.array([got[s] for s in samples])
+    scale = float(np.abs(f.psi).max())
+    assert np.abs(vals - want).max() <= 1e-5 * scale
+
+
+def test_rotation_blobs_full_size_invariants():
+    import torch
+    import paper_1507_01265_gb300 as mp
+    f = F.rotation_blobs()
+    dev = torch.device("cuda")
+    t = [torch.from_numpy(a).to(dev) for a in (f.h, f.psi, f.u1, f.u2, f.u3)]
+    with mp.Solver(f.nx, f.ny, f.nz, periodic=f.periodic) as s:
+        m0 = s.mass(t[0], t[1]).cpu().numpy()
+        s.step(*t, 20)
+        m1 = s.mass(t[0], t[1]).cpu().numpy()
+    assert abs(m1[0] / m0[0] - 1) <= 1e-5
+    assert m1[1] >= m0[1] - 1e-6 * m0[2] and m1[2] <= m0[2] * (1 + 1e-6)
