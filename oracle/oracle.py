@@ -4,13 +4,14 @@ from __future__ import annotations
 import ctypes
 import dataclasses
 import os
+import platform
 import subprocess
 
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "mpdata_oracle.c")
-_BUILD = os.path.join(_HERE, "_build")
+_BUILD = os.path.join(_HERE, "_build", platform.machine())
 _LIB = None
 
 

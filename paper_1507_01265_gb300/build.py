@@ -9,14 +9,17 @@ from __future__ import annotations
 import concurrent.futures as cf
 import glob
 import os
+import platform
 import subprocess
 import sys
 
 PKG = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
-BUILD = os.path.join(PKG, "_build")
+MACHINE = platform.machine()
+BUILD = os.path.join(PKG, "_build", MACHINE)  # objects never cross architectures
 LIB = os.path.join(PKG, "libmpdata.so")
+ARCH_MARK = LIB + ".arch"
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2", "-I", os.path.join(ROOT, "include"),
          "--expt-relaxed-constexpr"]
@@ -63,13 +66,16 @@ def build(force: bool = False, verbose: bool = False) -> str:
                     sys.stderr.write(r.stdout + r.stderr)
                 if r.returncode:
                     raise RuntimeError("nvcc failed: " + " ".join(cmd))
-    if force or jobs or _stale(LIB, objs):
+    mark = open(ARCH_MARK).read().strip() if os.path.exists(ARCH_MARK) else ""
+    if force or jobs or mark != MACHINE or _stale(LIB, objs):
         tmp = LIB + ".tmp%d" % os.getpid()
         cmd = [nvcc] + ARCH + ["-shared", "-o", tmp] + objs
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode:
             raise RuntimeError("link failed:\n" + r.stdout + r.stderr)
         os.replace(tmp, LIB)
+        with open(ARCH_MARK, "w") as fh:
+            fh.write(MACHINE + "\n")
     return LIB
 
 

@@ -12,8 +12,8 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 @pytest.fixture(scope="module")
 def mp():
-    from paper_1507_01265_gb300 import build as B
-    B.build()
+    import __graft_entry__ as g
+    g.build()
     import paper_1507_01265_gb300 as mp
     return mp
 
