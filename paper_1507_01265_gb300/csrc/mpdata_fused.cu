@@ -1,30 +1,32 @@
 // Fused MPDATA step: every stage of one time step in one kernel (§5.2's
-// 17 dependent stencil stages; the paper's (3+1)D decomposition in §5.3 keeps
+// dependent stencil stages; the paper's (3+1)D decomposition in §5.3 keeps
 // the intermediates of a block in cache -- here they live in shared memory
 // and registers, so a step moves only the 5 input fields and the output
 // through HBM).
 //
 // Decomposition (GB300-first, not the Xeon Phi code):
 //   * a CTA owns an output tile of TX x TY columns and marches it through all
-//     z planes; the z-neighbours of every quantity stay in registers as a
-//     short queue, the x/y neighbours go through shared-memory planes;
+//     z planes; every quantity a column needs from its own z-neighbours is
+//     carried in registers, x/y neighbours go through shared-memory planes;
 //   * each stage is evaluated on exactly the columns later stages need
-//     (psi1 on radius 2, pseudo-velocities on radius ~1.5, limiter factors
-//     on radius 1, limited fluxes on radius 0..1); thread t owns one column,
-//     columns are numbered from the tile outwards ring by ring, so every
-//     stage's region is a prefix of the thread index and idle threads form
-//     whole idle warps;
+//     (psi1 on radius 2, pseudo-velocities on radius ~1.5, limiter factors on
+//     radius 1, limited fluxes on radius 0..1).  Thread t owns one column and
+//     columns are numbered from the tile outwards ring by ring, so a stage's
+//     region is a prefix of the thread index and idle threads are whole warps;
 //   * inputs (psi, u1, u2, u3, h) of radius 3 stream into a 4-plane
 //     shared-memory ring with cp.async one plane ahead of use; the zero-fill
 //     form of cp.async supplies the zero velocity of lid faces;
-//   * per plane: donor pass (plane p-1) -> pseudo-velocities (plane p-2 and
-//     the z-face above it) -> limiter factors (p-2) -> limited fluxes and the
-//     finished output (plane p-3).
+//   * per plane p: donor pass at p-1 | pseudo-velocities of the x/y faces at
+//     p-2 | z-face pseudo-velocity above p-2 and limiter factors at p-2 |
+//     limited corrective fluxes at p-2 and the finished output at p-3.
 //
-// Boundary rules (the same readings as the oracle): periodic axes wrap; on a
-// lid axis faces 0 and n carry zero velocity and ghost cells are
-// zero-gradient copies (clamped neighbour reads in x/y, copied queue entries
-// in z).
+// Boundary rules (the oracle's readings): periodic axes wrap; on a lid axis
+// faces 0 and n carry zero velocity and ghost cells are zero-gradient copies
+// (clamped neighbour reads in x/y, copied queue entries in z).
+//
+// Arithmetic: FP32 divisions are a hardware reciprocal (rcp.approx, <= 1 ulp)
+// times the numerator, one reciprocal per denominator; FP64 keeps IEEE
+// reciprocals.  Local extrema use the 3-input min/max of sm_100+.
 #include "mpdata_internal.cuh"
 
 namespace mpdata {
@@ -38,7 +40,14 @@ struct Layout {
     static constexpr int N_VM = (TX + 1) * (TY + 1);
     static constexpr int N_BETA = (TX + 2) * (TY + 2);
     static constexpr int N_V = (TX + 3) * (TY + 3);
-    static constexpr int NPLANES = 5 * 4 + 8;  // input ring + psi1 x2, v1, v2, bup, bdn, gx, gy
+    // plane buffers (each PL elements)
+    static constexpr int RING = 0;    // 5 fields x 4 planes
+    static constexpr int P1 = 20;     // psi1, 2 planes
+    static constexpr int SX = 22;     // x-pair sums, 2 planes
+    static constexpr int SY = 24;     // y-pair sums, 2 planes
+    static constexpr int SZ = 26;     // z-pair sums of the face above q2
+    static constexpr int V1 = 27, V2 = 28, BU = 29, BD = 30, GX = 31, GY = 32;
+    static constexpr int NPLANES = 33;
     static_assert(PL <= 2 * NT, "each thread loads at most two columns");
 };
 
@@ -74,31 +83,55 @@ __device__ __forceinline__ int wrap_or_clamp(int a, int n, int per) {
 }
 
 template <typename T>
-__device__ __forceinline__ void cp_async(T *dst, const T *src, bool zero) {
-    unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+__device__ __forceinline__ void cp_async(unsigned dst, const T *src, bool zero) {
     int bytes = zero ? 0 : (int)sizeof(T);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;\n" ::"r"(d), "l"(src),
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;\n" ::"r"(dst), "l"(src),
                  "n"(sizeof(T)), "r"(bytes)
                  : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
 
-template <typename T>
-__device__ __forceinline__ T tmax(T a, T b) { return a > b ? a : b; }
-template <typename T>
-__device__ __forceinline__ T tmin(T a, T b) { return a < b ? a : b; }
+// Reciprocal: FP32 hardware approximation (<= 1 ulp), FP64 IEEE.
+__device__ __forceinline__ float rcp(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
 
-// Pseudo-velocity from its pieces:
+__device__ __forceinline__ float max3(float a, float b, float c) {
+    float r;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+__device__ __forceinline__ float min3(float a, float b, float c) {
+    float r;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+__device__ __forceinline__ double max3(double a, double b, double c) { return fmax(fmax(a, b), c); }
+__device__ __forceinline__ double min3(double a, double b, double c) { return fmin(fmin(a, b), c); }
+
+template <typename T>
+__device__ __forceinline__ T pos(T a) { return a > T(0) ? a : T(0); }
+template <typename T>
+__device__ __forceinline__ T neg(T a) { return a < T(0) ? a : T(0); }
+
+// Pseudo-velocity on a face from its pieces (pair sums s* across the face,
+// sums of the 4 transverse face velocities u*, h-sum of the two cells):
 //   V = (|U| - U^2/hbar) A - U (Ubar_a B_a + Ubar_b B_b) / hbar
+//   A = (pR - pL)/(pR + pL + eps), B = 1/2 (sp - sm)/(sp + sm + eps),
+//   Ubar = usum/4, hbar = hsum/2.
 template <typename T>
 __device__ __forceinline__ T pseudo_velocity(T U, T pR, T pL, T spa, T sma, T ua, T spb, T smb,
-                                             T ub, T h2sum, T eps) {
-    T A = (pR - pL) / (pR + pL + eps);
-    T Ba = T(0.5) * (spa - sma) / (spa + sma + eps);
-    T Bb = T(0.5) * (spb - smb) / (spb + smb + eps);
-    T hbar = T(0.5) * h2sum;
-    return (fabs(U) - U * U / hbar) * A - U * (T(0.25) * ua * Ba + T(0.25) * ub * Bb) / hbar;
+                                             T ub, T hsum, T eps) {
+    T A = (pR - pL) * rcp(pR + pL + eps);
+    T Ba = (spa - sma) * rcp(spa + sma + eps);
+    T Bb = (spb - smb) * rcp(spb + smb + eps);
+    T r = T(2) * rcp(hsum);             // 1/hbar
+    T cross = T(0.125) * (ua * Ba + ub * Bb);  // 1/4 (Ubar) x 1/2 (B)
+    return (fabs(U) - U * U * r) * A - U * cross * r;
 }
 
 template <typename T, int TX, int TY, bool NONOSC>
@@ -110,15 +143,9 @@ __global__ void __launch_bounds__(Layout<TX, TY>::NT, 1)
     constexpr int EX = L::EX, PL = L::PL, NT = L::NT;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *const sm = reinterpret_cast<T *>(smem_raw);
-    // plane buffers
-    T *const sV1 = sm + 22 * PL;
-    T *const sV2 = sm + 23 * PL;
-    T *const sBU = sm + 24 * PL;
-    T *const sBD = sm + 25 * PL;
-    T *const sGX = sm + 26 * PL;
-    T *const sGY = sm + 27 * PL;
-#define RING(f, q) (sm + ((f) * 4 + ((q) & 3)) * PL)
-#define P1(q) (sm + (20 + ((q) & 1)) * PL)
+    const unsigned sm_base = (unsigned)__cvta_generic_to_shared(sm);
+#define PLANE(k) (sm + (k) * PL)
+#define RING(f, q) PLANE(L::RING + (f) * 4 + ((q) & 3))
 
     const int t = threadIdx.x;
     const int nx = g.nx, ny = g.ny, nz = g.nz;
@@ -130,28 +157,27 @@ __global__ void __launch_bounds__(Layout<TX, TY>::NT, 1)
     int rx, ry;
     onion<TX, TY>(t, rx, ry);
     const int gx = x0 + rx, gy = y0 + ry;
-    const int ex = rx + 3, ey = ry + 3;
-    const int c0 = ey * EX + ex;
-    int exL = ex - 1, exR = ex + 1, eyD = ey - 1, eyU = ey + 1;  // clamped cell neighbours
-    if (!perx) { if (gx == 0) exL = ex; if (gx == nx - 1) exR = ex; }
-    if (!pery) { if (gy == 0) eyD = ey; if (gy == ny - 1) eyU = ey; }
-    const int cL = ey * EX + exL, cR = ey * EX + exR, cD = eyD * EX + ex, cU = eyU * EX + ex;
+    const int c0 = (ry + 3) * EX + (rx + 3);
+    // clamped cell neighbours (zero-gradient ghosts on lid axes)
+    const int cL = c0 - ((!perx && gx == 0) ? 0 : 1);
+    const int cR = c0 + ((!perx && gx == nx - 1) ? 0 : 1);
+    const int cD = c0 - ((!pery && gy == 0) ? 0 : EX);
+    const int cU = c0 + ((!pery && gy == ny - 1) ? 0 : EX);
     // lid faces of this column (zero velocity on its lower x / y face)
     const bool xlid = !perx && (gx <= 0 || gx >= nx);
     const bool ylid = !pery && (gy <= 0 || gy >= ny);
     const bool in_vm = t < L::N_VM, in_beta = t < L::N_BETA, in_v = t < L::N_V,
                in_out = t < L::N_OUT;
     const bool store = in_out && gx < nx && gy < ny;
+    T *const outp = out + (long long)gy * nx + gx;
 
     // ---- load columns: row-major over the radius-3 plane ----
     int ld_cell[2], ld_u1[2], ld_u2[2];
-    int nld = 0;
 #pragma unroll
     for (int r = 0; r < 2; ++r) {
         int c = t + r * NT;
         ld_cell[r] = ld_u1[r] = ld_u2[r] = -1;
         if (c < PL) {
-            ++nld;
             int lx = x0 - 3 + c % EX, ly = y0 - 3 + c / EX;
             int cx = wrap_or_clamp(lx, nx, perx), cy = wrap_or_clamp(ly, ny, pery);
             ld_cell[r] = cy * nx + cx;
@@ -164,176 +190,162 @@ __global__ void __launch_bounds__(Layout<TX, TY>::NT, 1)
     auto issue = [&](int p) {
         const long long pc = (long long)wrap_or_clamp(p, nz, perz) * nxy;
         const bool zz = !perz && (p <= 0 || p >= nz);  // lid z-face
+        const unsigned slot = (unsigned)(p & 3) * PL;
 #pragma unroll
         for (int r = 0; r < 2; ++r) {
-            if (r < nld) {
-                int c = t + r * NT;
+            const int c = t + r * NT;
+            if (c < PL) {
+                const unsigned d = sm_base + (unsigned)(slot + c) * (unsigned)sizeof(T);
+                const unsigned fs = 4u * PL * (unsigned)sizeof(T);  // field stride
                 const long long o = pc + ld_cell[r];
-                cp_async(RING(0, p) + c, psi + o, false);
-                cp_async(RING(1, p) + c, ld_u1[r] < 0 ? u1 : u1 + pc + ld_u1[r], ld_u1[r] < 0);
-                cp_async(RING(2, p) + c, ld_u2[r] < 0 ? u2 : u2 + pc + ld_u2[r], ld_u2[r] < 0);
-                cp_async(RING(3, p) + c, zz ? u3 : u3 + o, zz);
-                cp_async(RING(4, p) + c, h + o, false);
+                cp_async(d, psi + o, false);
+                cp_async(d + fs, ld_u1[r] < 0 ? u1 : u1 + pc + ld_u1[r], ld_u1[r] < 0);
+                cp_async(d + 2 * fs, ld_u2[r] < 0 ? u2 : u2 + pc + ld_u2[r], ld_u2[r] < 0);
+                cp_async(d + 3 * fs, zz ? u3 : u3 + o, zz);
+                cp_async(d + 4 * fs, h + o, false);
             }
         }
         cp_async_commit();
     };
 
-    // ---- z range (periodic z also evaluates the wrap planes around the ends) ----
+    // ---- z range (periodic z also evaluates wrap planes around the ends) ----
     const int p_first = perz ? -3 : -1;
     const int p_last = nz + 2;
     const int q1lo = perz ? -2 : 0, q1hi = perz ? nz + 1 : nz - 1;
+    const int q1top = perz ? q1hi : nz;                        // lid: plane nz is a ghost copy
     const int wlo = perz ? -2 : 0, whi = perz ? nz : nz - 2;   // z-face above plane q2
     const int vlo = perz ? -1 : 0, vhi = perz ? nz : nz - 1;   // V1, V2, beta at plane q2
 
-    // ---- register queues along z ----
-    T p1a = T(0), p1b = T(0);        // psi1 at q2-1, q2
-    T sxa = T(0), sxb = T(0);        // x-pair sums at q2-1, q2
-    T sya = T(0), syb = T(0);        // y-pair sums
-    T wlo_v = T(0);                  // pseudo-velocity on the z-face below q2
-    T bu_prev = T(0), bd_prev = T(0);// limiter factors at q2-1
-    T pn_prev = T(0);                // psi^n at q2-1
-    T h_prev = T(1);                 // h at q3
-    T dacc = T(0);                   // partial divergence of the output plane
-    T gx_own = T(0), gy_own = T(0);  // own lower-face corrective fluxes (previous plane)
-    T v1_own = T(0), v2_own = T(0);
+    // ---- own-column queues along z ----
+    T pn_mm = T(0), pn_m = T(0), pn_c = T(0);  // psi^n at q2-1, q2 (=q1-1), q1
+    T p1a = T(0), p1b = T(0);                  // psi1 at q2-1, q2
+    T sxa = T(0), sxb = T(0), sya = T(0), syb = T(0);  // pair sums at q2-1, q2
+    T u1b = T(0), u2b = T(0), u3b = T(0), hb = T(1);   // inputs at q2
+    T u3c = T(0);                              // u3 on the lower face of q1
+    T wlo_v = T(0);                            // z-face pseudo-velocity below q2
+    T bu_prev = T(0), bd_prev = T(0);          // limiter factors at q2-1
+    T h_prev = T(1), p1_prev = T(0);           // h, psi1 at q3
+    T dacc = T(0), gx_own = T(0), gy_own = T(0);
 
     issue(p_first);
     for (int p = p_first; p <= p_last; ++p) {
         const int q1 = p - 1, q2 = p - 2, q3 = p - 3;
         if (p + 1 <= p_last) issue(p + 1); else cp_async_commit();
         cp_async_wait_1();
-        __syncthreads();  // (A) plane p landed; previous iteration's fluxes visible
+        __syncthreads();  // (A) plane p landed; fluxes of the previous iteration visible
 
-        // deferred: finish the x/y divergence of plane q3 (fluxes of the previous iteration)
+        // deferred: x/y part of the corrective divergence of plane q3
         if (in_out && q3 >= 0 && q3 <= nz - 1) {
-            T gxr = sGX[c0 + 1], gyu = sGY[c0 + EX];
+            const T gxr = PLANE(L::GX)[c0 + 1], gyu = PLANE(L::GY)[c0 + EX];
             dacc = ((gxr - gx_own) + (gyu - gy_own)) + dacc;
         }
 
-        // (a1) donor-cell pass at plane q1
-        T p1c = p1b;  // lid top ghost: zero-gradient copy
+        // ---- (a1) donor-cell pass at plane q1 (all threads: radius 2) ----
+        const T *Pn = RING(0, q1);
+        const T pn_p = RING(0, p)[c0];
+        const T u3p = RING(3, p)[c0];
+        const T u1c = RING(1, q1)[c0], u2c = RING(2, q1)[c0], hc = RING(4, q1)[c0];
+        T p1c = p1b;  // lid top ghost: zero-gradient copy of the plane below
         if (q1 >= q1lo && q1 <= q1hi) {
-            const T *pm = RING(0, q1 - 1), *pc = RING(0, q1), *pp = RING(0, q1 + 1);
-            const T *U1 = RING(1, q1), *U2 = RING(2, q1), *U3c = RING(3, q1),
-                    *U3p = RING(3, q1 + 1);
-            T ps = pc[c0];
-            T fxl = upstream_flux(U1[c0], pc[c0 - 1], ps);
-            T fxh = upstream_flux(U1[c0 + 1], ps, pc[c0 + 1]);
-            T fyl = upstream_flux(U2[c0], pc[c0 - EX], ps);
-            T fyh = upstream_flux(U2[c0 + EX], ps, pc[c0 + EX]);
-            T fzl = upstream_flux(U3c[c0], pm[c0], ps);
-            T fzh = upstream_flux(U3p[c0], ps, pp[c0]);
-            T div = (fxh - fxl) + (fyh - fyl) + (fzh - fzl);
-            p1c = ps - div / RING(4, q1)[c0];
+            const T fxl = upstream_flux(u1c, Pn[c0 - 1], pn_c);
+            const T fxh = upstream_flux(RING(1, q1)[c0 + 1], pn_c, Pn[c0 + 1]);
+            const T fyl = upstream_flux(u2c, Pn[c0 - EX], pn_c);
+            const T fyh = upstream_flux(RING(2, q1)[c0 + EX], pn_c, Pn[c0 + EX]);
+            const T fzl = upstream_flux(u3c, pn_m, pn_c);
+            const T fzh = upstream_flux(u3p, pn_c, pn_p);
+            const T div = (fxh - fxl) + (fyh - fyl) + (fzh - fzl);
+            p1c = pn_c - div * rcp(hc);
         }
-        if (q1 >= q1lo && q1 <= (perz ? q1hi : nz)) P1(q1)[c0] = p1c;
-        __syncthreads();  // (D) psi1 plane q1 visible
+        if (q1 >= q1lo && q1 <= q1top) PLANE(L::P1 + (q1 & 1))[c0] = p1c;
+        __syncthreads();  // (D) psi1 of plane q1 visible
 
-        // own h and psi^n at q2, read now: after the last barrier of this
-        // iteration other threads may already stream plane p+2 into this slot
-        const T h_q2 = RING(4, q2)[c0], pn_q2 = RING(0, q2)[c0];
-
-        // (a2) pseudo-velocities: lower x/y faces at q2, z-face between q2 and q1
-        T sxc = sxb, syc = syb, whi_v = T(0);
+        // ---- (a2) pseudo-velocities of the lower x/y faces at q2 ----
+        const T *Pb = PLANE(L::P1 + (q2 & 1));
+        const T *Pc = PLANE(L::P1 + (q1 & 1));
+        T sxc = sxb, syc = syb;
+        T v1_own = T(0), v2_own = T(0);
+        T pl = T(0), pd = T(0);
+        // pair sums across the lower x/y faces at q1 and across the z-face
+        // between q2 and q1 (all threads: the cross terms read them one row
+        // or column outside the pseudo-velocity region)
+        if (q1 >= q1lo && q1 <= q1top) {
+            sxc = Pc[c0 - 1] + p1c;
+            syc = Pc[c0 - EX] + p1c;
+            PLANE(L::SX + (q1 & 1))[c0] = sxc;
+            PLANE(L::SY + (q1 & 1))[c0] = syc;
+            PLANE(L::SZ)[c0] = p1b + p1c;
+        }
+        if (!perz && q1 == 0) { p1b = p1c; sxb = sxc; syb = syc; }  // lid bottom ghost
         if (in_v) {
-            const T *Pb = P1(q2), *Pc = P1(q1);
-            const bool q1ok = q1 >= q1lo && q1 <= (perz ? q1hi : nz);
-            if (q1ok) {
-                sxc = Pc[c0 - 1] + p1c;
-                syc = Pc[c0 - EX] + p1c;
-            }
-            if (!perz && q1 == 0) { p1b = p1c; sxb = sxc; syb = syc; }  // lid bottom ghost
             if (q2 >= vlo && q2 <= vhi) {
                 const T *U1b = RING(1, q2), *U2b = RING(2, q2), *U3b = RING(3, q2),
                         *U3c = RING(3, q1), *Hb = RING(4, q2);
-                const T pb = p1b;
-                // x-face
-                {
-                    T U = U1b[c0];
-                    T pl = Pb[c0 - 1];
-                    T spa = Pb[cU] + Pb[cU - 1], sma = Pb[cD] + Pb[cD - 1];
-                    T ua = U2b[c0 - 1] + U2b[c0] + U2b[c0 - 1 + EX] + U2b[c0 + EX];
-                    T ub = U3b[c0 - 1] + U3b[c0] + U3c[c0 - 1] + U3c[c0];
-                    T v = pseudo_velocity(U, pb, pl, spa, sma, ua, sxc, sxa, ub,
-                                          Hb[c0 - 1] + Hb[c0], eps);
-                    v1_own = xlid ? T(0) : v;
-                }
-                // y-face
-                {
-                    T U = U2b[c0];
-                    T pd = Pb[c0 - EX];
-                    T ua = U3b[c0 - EX] + U3b[c0] + U3c[c0 - EX] + U3c[c0];
-                    T spb = Pb[cR] + Pb[cR - EX], smb = Pb[cL] + Pb[cL - EX];
-                    T ub = U1b[c0 - EX] + U1b[c0] + U1b[c0 + 1 - EX] + U1b[c0 + 1];
-                    T v = pseudo_velocity(U, pb, pd, syc, sya, ua, spb, smb, ub,
-                                          Hb[c0 - EX] + Hb[c0], eps);
-                    v2_own = ylid ? T(0) : v;
-                }
-                sV1[c0] = v1_own;
-                sV2[c0] = v2_own;
+                const T *Sxb = PLANE(L::SX + (q2 & 1)), *Syb = PLANE(L::SY + (q2 & 1));
+                pl = Pb[c0 - 1];
+                pd = Pb[c0 - EX];
+                // x-face: B_y from the x-pair sums of the rows above/below, B_z from own queue
+                const T ua = U2b[c0 - 1] + u2b + U2b[c0 - 1 + EX] + U2b[c0 + EX];
+                const T ub = U3b[c0 - 1] + u3b + U3c[c0 - 1] + u3c;
+                const T v1 = pseudo_velocity(u1b, p1b, pl, Sxb[cU], Sxb[cD], ua, sxc, sxa, ub,
+                                             Hb[c0 - 1] + hb, eps);
+                // y-face: B_z from own queue, B_x from the y-pair sums of the columns left/right
+                const T va = U3b[c0 - EX] + u3b + U3c[c0 - EX] + u3c;
+                const T vb = U1b[c0 - EX] + u1b + U1b[c0 + 1 - EX] + U1b[c0 + 1];
+                const T v2 = pseudo_velocity(u2b, p1b, pd, syc, sya, va, Syb[cR], Syb[cL], vb,
+                                             Hb[c0 - EX] + hb, eps);
+                v1_own = xlid ? T(0) : v1;
+                v2_own = ylid ? T(0) : v2;
+                PLANE(L::V1)[c0] = v1_own;
+                PLANE(L::V2)[c0] = v2_own;
             }
+        }
+        __syncthreads();  // (F) V1, V2, pair sums of plane q2 visible
+
+        // ---- (a2) z-face above q2, then (a3)+(a4) extrema and limiter factors ----
+        T whi_v = T(0), bu_c = T(0), bd_c = T(0);
+        if (in_beta) {
             if (q2 >= wlo && q2 <= whi) {
-                const T *U1b = RING(1, q2), *U2b = RING(2, q2), *U1c = RING(1, q1),
-                        *U2c = RING(2, q1);
-                T U = RING(3, q1)[c0];
-                T spa = Pc[cR] + Pb[cR], sma = Pc[cL] + Pb[cL];
-                T ua = U1b[c0] + U1c[c0] + U1b[c0 + 1] + U1c[c0 + 1];
-                T spb = Pc[cU] + Pb[cU], smb = Pc[cD] + Pb[cD];
-                T ub = U2b[c0] + U2c[c0] + U2b[c0 + EX] + U2c[c0 + EX];
-                whi_v = pseudo_velocity(U, p1c, p1b, spa, sma, ua, spb, smb, ub,
-                                        RING(4, q2)[c0] + RING(4, q1)[c0], eps);
+                const T *Sz = PLANE(L::SZ);
+                const T *U1b = RING(1, q2), *U2b = RING(2, q2);
+                const T ua = u1b + u1c + U1b[c0 + 1] + RING(1, q1)[c0 + 1];
+                const T ub = u2b + u2c + U2b[c0 + EX] + RING(2, q1)[c0 + EX];
+                whi_v = pseudo_velocity(u3c, p1c, p1b, Sz[cR], Sz[cL], ua, Sz[cU], Sz[cD], ub,
+                                        hb + hc, eps);
+            }
+            if (NONOSC && q2 >= vlo && q2 <= vhi) {
+                const T *Pnb = RING(0, q2);
+                const T aL = Pnb[cL], aR = Pnb[cR], aD = Pnb[cD], aU = Pnb[cU];
+                const T bL = Pb[cL], bR = Pb[cR], bD = Pb[cD], bU = Pb[cU];
+                T mx = max3(max3(aL, aR, aD), max3(aU, bL, bR), max3(bD, bU, pn_mm));
+                mx = max3(mx, max3(pn_m, pn_c, p1a), max3(p1b, p1c, p1b));
+                T mn = min3(min3(aL, aR, aD), min3(aU, bL, bR), min3(bD, bU, pn_mm));
+                mn = min3(mn, min3(pn_m, pn_c, p1a), min3(p1b, p1c, p1b));
+                const T v1h = PLANE(L::V1)[c0 + 1], v2h = PLANE(L::V2)[c0 + EX];
+                const T in = (pos(v1_own) * bL - neg(v1h) * bR) + (pos(v2_own) * bD - neg(v2h) * bU) +
+                             (pos(wlo_v) * p1a - neg(whi_v) * p1c);
+                const T outf = ((pos(v1h) - neg(v1_own)) + (pos(v2h) - neg(v2_own)) +
+                                (pos(whi_v) - neg(wlo_v))) * p1b;
+                bu_c = (mx - p1b) * hb * rcp(in + eps);
+                bd_c = (p1b - mn) * hb * rcp(outf + eps);
+                PLANE(L::BU)[c0] = bu_c;
+                PLANE(L::BD)[c0] = bd_c;
             }
         }
-        __syncthreads();  // (F) V1, V2 of plane q2 visible
+        __syncthreads();  // (H) limiter factors of q2 visible; ring slot q2 free for reuse
 
-        // (a3)+(a4) local extrema and limiter factors at q2
-        T bu_c = T(0), bd_c = T(0);
-        if (NONOSC) {
-            if (in_beta && q2 >= vlo && q2 <= vhi) {
-                const T *Pn = RING(0, q2), *Pb = P1(q2);
-                T pnc = Pn[c0], pnu = RING(0, q1)[c0];
-                T mx = tmax(tmax(pnc, p1b), tmax(pn_prev, pnu));
-                T mn = tmin(tmin(pnc, p1b), tmin(pn_prev, pnu));
-                mx = tmax(mx, tmax(p1a, p1c));
-                mn = tmin(mn, tmin(p1a, p1c));
-                T aL = Pn[cL], aR = Pn[cR], aD = Pn[cD], aU = Pn[cU];
-                T bL = Pb[cL], bR = Pb[cR], bD = Pb[cD], bU = Pb[cU];
-                mx = tmax(mx, tmax(tmax(aL, aR), tmax(aD, aU)));
-                mx = tmax(mx, tmax(tmax(bL, bR), tmax(bD, bU)));
-                mn = tmin(mn, tmin(tmin(aL, aR), tmin(aD, aU)));
-                mn = tmin(mn, tmin(tmin(bL, bR), tmin(bD, bU)));
-                T v1h = sV1[c0 + 1], v2h = sV2[c0 + EX];
-                T in = (tmax(v1_own, T(0)) * bL - tmin(v1h, T(0)) * bR) +
-                       (tmax(v2_own, T(0)) * bD - tmin(v2h, T(0)) * bU) +
-                       (tmax(wlo_v, T(0)) * p1a - tmin(whi_v, T(0)) * p1c);
-                T outf = ((tmax(v1h, T(0)) - tmin(v1_own, T(0))) +
-                          (tmax(v2h, T(0)) - tmin(v2_own, T(0))) +
-                          (tmax(whi_v, T(0)) - tmin(wlo_v, T(0)))) * p1b;
-                T hc = RING(4, q2)[c0];
-                bu_c = (mx - p1b) * hc / (in + eps);
-                bd_c = (p1b - mn) * hc / (outf + eps);
-                sBU[c0] = bu_c;
-                sBD[c0] = bd_c;
-            }
-            __syncthreads();  // (H) limiter factors of plane q2 visible
-        }
-
-        // (a5)+(a6) limited velocities, corrective fluxes, and the output of plane q3
+        // ---- (a5)+(a6) limited corrective fluxes at q2, output of plane q3 ----
         if (in_vm && q2 >= 0 && q2 <= nz - 1) {
-            const T *Pb = P1(q2);
             T vm1 = v1_own, vm2 = v2_own;
             if (NONOSC) {
-                T buL = sBU[c0 - 1], bdL = sBD[c0 - 1], buD = sBU[c0 - EX], bdD = sBD[c0 - EX];
-                vm1 = tmax(v1_own, T(0)) * tmin(T(1), tmin(bdL, bu_c)) +
-                      tmin(v1_own, T(0)) * tmin(T(1), tmin(buL, bd_c));
-                vm2 = tmax(v2_own, T(0)) * tmin(T(1), tmin(bdD, bu_c)) +
-                      tmin(v2_own, T(0)) * tmin(T(1), tmin(buD, bd_c));
+                const T *Bu = PLANE(L::BU), *Bd = PLANE(L::BD);
+                const T buL = Bu[c0 - 1], bdL = Bd[c0 - 1], buD = Bu[c0 - EX], bdD = Bd[c0 - EX];
+                vm1 = pos(v1_own) * min3(T(1), bdL, bu_c) + neg(v1_own) * min3(T(1), buL, bd_c);
+                vm2 = pos(v2_own) * min3(T(1), bdD, bu_c) + neg(v2_own) * min3(T(1), buD, bd_c);
             }
-            gx_own = xlid ? T(0) : upstream_flux(vm1, Pb[c0 - 1], p1b);
-            gy_own = ylid ? T(0) : upstream_flux(vm2, Pb[c0 - EX], p1b);
-            sGX[c0] = gx_own;
-            sGY[c0] = gy_own;
+            gx_own = xlid ? T(0) : upstream_flux(vm1, pl, p1b);
+            gy_own = ylid ? T(0) : upstream_flux(vm2, pd, p1b);
+            PLANE(L::GX)[c0] = gx_own;
+            PLANE(L::GY)[c0] = gy_own;
         }
         const bool q3ok = q3 >= 0 && q3 <= nz - 1, q2ok = q2 >= 0 && q2 <= nz - 1;
         if (in_out && (q3ok || q2ok)) {
@@ -342,33 +354,37 @@ __global__ void __launch_bounds__(Layout<TX, TY>::NT, 1)
             if (perz || (q2 >= 1 && q2 <= nz - 1)) {
                 T vm3 = wlo_v;
                 if (NONOSC)
-                    vm3 = tmax(wlo_v, T(0)) * tmin(T(1), tmin(bd_prev, bu_c)) +
-                          tmin(wlo_v, T(0)) * tmin(T(1), tmin(bu_prev, bd_c));
+                    vm3 = pos(wlo_v) * min3(T(1), bd_prev, bu_c) + neg(wlo_v) * min3(T(1), bu_prev, bd_c);
                 gz = upstream_flux(vm3, p1a, p1b);
             }
-            if (q3ok) {
-                T res = p1a - (dacc + gz) / h_prev;
-                if (store) out[(long long)q3 * nxy + (long long)gy * nx + gx] = res;
-            }
+            if (q3ok && store) outp[(long long)q3 * nxy] = p1_prev - (dacc + gz) * rcp(h_prev);
             dacc = -gz;  // lower z-face flux of plane q2; x/y parts are added next iteration
         }
 
-        // shift the queues
-        h_prev = h_q2;
-        pn_prev = pn_q2;
+        // ---- shift the queues ----
+        h_prev = hb;
+        p1_prev = p1b;
+        pn_mm = pn_m;
+        pn_m = pn_c;
+        pn_c = pn_p;
         p1a = p1b;
         p1b = p1c;
         sxa = sxb;
         sxb = sxc;
         sya = syb;
         syb = syc;
+        u1b = u1c;
+        u2b = u2c;
+        u3b = u3c;
+        u3c = u3p;
+        hb = hc;
         wlo_v = whi_v;
         bu_prev = bu_c;
         bd_prev = bd_c;
     }
     asm volatile("cp.async.wait_all;\n" ::: "memory");
 #undef RING
-#undef P1
+#undef PLANE
 }
 
 template <typename T, int TX, int TY>
@@ -390,7 +406,8 @@ cudaError_t launch_tile(const Grid &g, int nonosc, double eps, const void *h, co
 
 bool fused_tile_supported(int dtype, int tx, int ty) {
     if (dtype == MPDATA_F64) return (tx == 16 && ty == 16);
-    return (tx == 32 && ty == 16) || (tx == 24 && ty == 24) || (tx == 16 && ty == 16);
+    return (tx == 32 && ty == 16) || (tx == 24 && ty == 24) || (tx == 16 && ty == 16) ||
+           (tx == 24 && ty == 16);
 }
 
 void fused_default_tile(int dtype, int *tx, int *ty) {
@@ -410,6 +427,8 @@ cudaError_t launch_fused_step(int dtype, const Grid &g, int nonosc, double eps, 
         return launch_tile<float, 32, 16>(g, nonosc, eps, h, psi, u1, u2, u3, out, s);
     if (tx == 24 && ty == 24)
         return launch_tile<float, 24, 24>(g, nonosc, eps, h, psi, u1, u2, u3, out, s);
+    if (tx == 24 && ty == 16)
+        return launch_tile<float, 24, 16>(g, nonosc, eps, h, psi, u1, u2, u3, out, s);
     if (tx == 16 && ty == 16)
         return launch_tile<float, 16, 16>(g, nonosc, eps, h, psi, u1, u2, u3, out, s);
     return cudaErrorInvalidValue;
