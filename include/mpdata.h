@@ -108,6 +108,33 @@ int mpdata_solve_host(mpdata_t *handle, const void *h, void *psi, const void *u1
  * Errors: EINVAL, ECUDA. */
 int mpdata_mass(mpdata_t *handle, const void *h, const void *psi, void *out3, void *stream);
 
+/* mpdata_mass without a handle and without any device allocation, for
+ * callers that cannot allocate device memory themselves: code embedded in a
+ * host framework whose allocator owns all device memory and forbids raw
+ * cudaMalloc, services that budget every allocation up front, and loops
+ * that cannot afford the implicit synchronisation of cudaMalloc/cudaFree.
+ * (The paper has no counterpart; this is a library-integration entry point.)
+ *
+ * Computes the same three doubles as mpdata_mass (sum h*psi in FP64 with the
+ * same fixed reduction tree, min psi, max psi) over n elements of dtype
+ * (MPDATA_F32 or MPDATA_F64) into the DEVICE pointer out3, async on stream.
+ * h and psi are device pointers (16-byte aligned), out3 is 8-byte aligned;
+ * the caller still provides all inputs and outputs.
+ *
+ * Scratch: the reduction partials live in a fixed static device array of
+ * 3 x 1024 doubles (24 KiB) inside the library, held by every GPU that
+ * loads it until the process exits; no cudaMalloc, cudaFree or other
+ * allocating call is made.  Limit: n must be in [1, 2^31 - 1] (EINVAL
+ * otherwise).  The first call on each device looks up the array's device
+ * address (cudaGetSymbolAddress) with that device current; make that first
+ * call before any stream capture.  All calls share the one array and every
+ * call overwrites all partials it reads, so nothing has to start at zero --
+ * but calls whose kernels overlap on the GPU (other streams, other threads)
+ * race on it and must be serialised by the caller.
+ * Errors: EINVAL, ECUDA. */
+int mpdata_mass_noalloc(const void *h, const void *psi, long long n, int dtype, void *out3,
+                        void *stream);
+
 /* Name of an error code. */
 const char *mpdata_strerror(int code);
 

@@ -55,6 +55,7 @@ def _load():
         "mpdata_step": (I, [H, P, P, P, P, P, I, P]),
         "mpdata_solve_host": (I, [H, P, P, P, P, P, I, P]),
         "mpdata_mass": (I, [H, P, P, P, P]),
+        "mpdata_mass_noalloc": (I, [P, P, ctypes.c_longlong, I, P, P]),
         "mpdata_strerror": (ctypes.c_char_p, [I]),
         "mpdata_last_error_message": (ctypes.c_char_p, []),
         "mpdata_version": (ctypes.c_char_p, []),

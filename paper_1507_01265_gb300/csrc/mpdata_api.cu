@@ -219,6 +219,20 @@ int mpdata_mass(mpdata_t *m, const void *h, const void *psi, void *out3, void *s
     return e == cudaSuccess ? MPDATA_OK : cuda_fail(e, "mass kernel launch");
 }
 
+int mpdata_mass_noalloc(const void *h, const void *psi, long long n, int dtype, void *out3,
+                        void *stream) {
+    if (n < 1 || n >= (1LL << 31))
+        return fail(MPDATA_EINVAL, "n = %lld is outside [1, 2^31 - 1], the largest grid this entry point accepts", n);
+    if (dtype != MPDATA_F32 && dtype != MPDATA_F64) return fail(MPDATA_EINVAL, "dtype must be MPDATA_F32 or MPDATA_F64");
+    if (!aligned16(h) || !aligned16(psi)) return fail(MPDATA_EINVAL, "h or psi is NULL or not 16-byte aligned");
+    if (!out3 || ((uintptr_t)out3 & 7u)) return fail(MPDATA_EINVAL, "out3 is NULL or not 8-byte aligned");
+    double *partials = nullptr;
+    cudaError_t e = mpdata::noalloc_partials(&partials);
+    if (e != cudaSuccess) return cuda_fail(e, "static scratch lookup (cudaGetSymbolAddress)");
+    e = mpdata::launch_mass(dtype, n, h, psi, partials, (double *)out3, (cudaStream_t)stream);
+    return e == cudaSuccess ? MPDATA_OK : cuda_fail(e, "mass kernel launch");
+}
+
 const char *mpdata_strerror(int code) {
     switch (code) {
     case MPDATA_OK: return "ok";

@@ -53,5 +53,8 @@ void fused_default_tile(int dtype, int *tile_x, int *tile_y);
 constexpr int kReduceBlocks = 1024;  // fixed, so the summation tree never changes
 cudaError_t launch_mass(int dtype, long long n, const void *h, const void *psi, double *partials,
                         double *out3, cudaStream_t s);
+// Device address of the static partials array of mpdata_mass_noalloc on the
+// current device (looked up on the first call per device).
+cudaError_t noalloc_partials(double **out);
 
 }  // namespace mpdata

@@ -7,6 +7,8 @@
 // run to run (and independent of the launch order of the blocks).
 #include <float.h>
 
+#include <mutex>
+
 #include "mpdata_internal.cuh"
 
 namespace mpdata {
@@ -71,7 +73,34 @@ __global__ void k_mass_final(int nparts, const double *__restrict__ part, double
     }
 }
 
+// Scratch of mpdata_mass_noalloc: the per-block partials live in this
+// file-scope device array instead of a cudaMalloc'd buffer.  Every GPU that
+// loads the library holds it (24 KiB) until the process exits.  In host code
+// the name is only a stand-in; its device address comes from
+// cudaGetSymbolAddress, looked up once per device.
+static __device__ __align__(256) double g_noalloc_partials[3 * kReduceBlocks];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+double *g_noalloc_ptr[kMaxDevices];
+
 }  // namespace
+
+cudaError_t noalloc_partials(double **out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_partials);  // this device is current
+        if (e != cudaSuccess) return e;
+        g_noalloc_ptr[dev] = (double *)p;
+    }
+    *out = g_noalloc_ptr[dev];
+    return cudaSuccess;
+}
 
 cudaError_t launch_mass(int dtype, long long n, const void *h, const void *psi, double *partials,
                         double *out3, cudaStream_t s) {
