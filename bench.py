@@ -14,8 +14,8 @@ Prints ONE JSON line (rank 0):
   cpu_baseline  the FP64 oracle on a bounded sample of the same workload
   clocks     nvidia-smi samples taken during the timed region
 
---impl reference times the oracle itself (the CPU reference of this build)
-on a bounded sample per step.  Under torchrun (N > 1) every rank runs its own
+--impl reference times the FP64 oracle (the serial CPU reference) on a
+bounded sample per step.  Under torchrun (N > 1) every rank runs its own
 replica of the problem (the workload does not shard across GPUs here).
 """
 from __future__ import annotations
@@ -141,46 +141,60 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def oracle_sample(seconds_hint=15.0):
-    """Time the FP64 oracle, as it stands, on a bounded sample of the
-    workload: the first `rows` y-rows of the 1024x512x64 grid for one step
-    (one host core)."""
+def oracle_setup(rows):
+    """A slab of the first `rows` y-rows of the 1024x512x64 workload, as
+    float64 arrays for the oracle."""
     import numpy as np
     import gen.fields as F
     import oracle
-    rows = 64 if seconds_hint >= 10 else 16
     f = F.rotation_blobs()
     sub = lambda a: np.ascontiguousarray(a[:, :rows, :], dtype=np.float64)
-    h, psi, u1, u2, u3 = (sub(a) for a in (f.h, f.psi, f.u1, f.u2, f.u3))
-    cfg = oracle.Config(f.nx, rows, f.nz, (1, 1, 0))
+    arrs = tuple(sub(a) for a in (f.h, f.psi, f.u1, f.u2, f.u3))
     oracle.load()
+    return oracle.Config(f.nx, rows, f.nz, (1, 1, 0)), arrs
+
+
+def oracle_time(cfg, arrs):
+    """Seconds for one oracle step on the slab (serial FP64 C, one core)."""
+    import oracle
     t0 = time.perf_counter()
-    oracle.run(cfg, h, psi, u1, u2, u3, nsteps=1)
-    dt = time.perf_counter() - t0
-    cells = f.nx * rows * f.nz
+    oracle.run(cfg, *arrs, nsteps=1)
+    return time.perf_counter() - t0
+
+
+def oracle_sample(rows=64):
+    """Time the FP64 oracle, as it stands, on a bounded sample of the
+    workload: one step of the first `rows` y-rows of the 1024x512x64 grid."""
+    cfg, arrs = oracle_setup(rows)
+    dt = oracle_time(cfg, arrs)
+    cells = cfg.nx * cfg.ny * cfg.nz
     return {"value": cells / dt / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": "1 step of a %dx%dx%d slab (first %d y-rows) of the 1024x512x64 workload, "
-                      "serial FP64 C, %.1f s" % (f.nx, rows, f.nz, rows, dt)}
+                      "serial FP64 C, %.1f s" % (cfg.nx, rows, cfg.nz, rows, dt)}
 
 
 def run_reference(args, rank, world):
+    """The oracle as the reference arm: each bench step is one oracle step on
+    a 1024x16x64 slab of the same workload."""
     if rank != 0:
         return 0
-    import gen.fields as F  # noqa: F401
-    times = []
-    info = None
-    for i in range(args.warmup + args.steps):
-        r = oracle_sample(seconds_hint=2.0)
-        if i >= args.warmup:
-            times.append(r["value"])
-        info = r
-    v = statistics.mean(times)
+    rows = 16
+    cfg, arrs = oracle_setup(rows)
+    cells = cfg.nx * cfg.ny * cfg.nz
+    for _ in range(args.warmup):
+        oracle_time(cfg, arrs)
+    times = [oracle_time(cfg, arrs) for _ in range(args.steps)]
+    t = sum(times)
+    v = cells * len(times) / t / 1e9
+    sample = ("each step: 1 step of a %dx%dx%d slab (first %d y-rows) of the 1024x512x64 "
+              "workload, serial FP64 C" % (cfg.nx, rows, cfg.nz, rows))
     line = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-            "config": {"workload": "rotation_blobs 1024x512x64 (sampled slab)", "grid": [NX, NY, NZ]},
-            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": info["sample"]},
+            "warmup": args.warmup, "ms_per_step": 1e3 * t / len(times), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": "rotation_blobs 1024x512x64, periodic x/y, lid z (sampled slab)",
+                       "grid": [NX, NY, NZ], "sample_grid": [cfg.nx, rows, cfg.nz]},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0

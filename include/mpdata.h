@@ -2,8 +2,8 @@
  * mpdata.h -- C ABI of the GB300 (sm_103a) MPDATA advection library.
  *
  * One MPDATA time step advances a scalar psi carried by a density h and
- * staggered Courant numbers u1, u2, u3: the step reads these 5 matrices and
- * returns 1 (the paper, §5.2: "5 input matrices ... one output matrix").
+ * staggered Courant numbers u1, u2, u3: each step reads these five fields and
+ * produces one (§5.2).
  * The step is the nonoscillatory forward-in-time scheme the paper refers to
  * in §5.2: a donor-cell (upstream) pass, antidiffusive pseudo-velocities with
  * cross terms, the nonoscillatory limiter (local extrema as in Listing 1,
