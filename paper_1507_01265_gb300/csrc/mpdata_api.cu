@@ -116,10 +116,13 @@ int mpdata_create(int nx, int ny, int nz, const mpdata_opts *opts, mpdata_t **ou
     if (opts) o = *opts; else mpdata_opts_default(&o);
     int rc = check_opts(&o);
     if (rc) return rc;
+    Grid grid;
+    grid.nx = nx; grid.ny = ny; grid.nz = nz;
+    for (int d = 0; d < 3; ++d) grid.per[d] = o.periodic[d];
     int tx = o.tile_x, ty = o.tile_y;
-    if (tx == 0 && ty == 0) mpdata::fused_default_tile(o.dtype, &tx, &ty);
-    if (o.path == MPDATA_PATH_FUSED && o.iterations == 2 && !mpdata::fused_tile_supported(o.dtype, tx, ty))
-        return fail(MPDATA_EINVAL, "no fused kernel for tile %d x %d", tx, ty);
+    if (tx == 0 && ty == 0) mpdata::fused_default_tile(o.dtype, grid, &tx, &ty);
+    if (o.path == MPDATA_PATH_FUSED && o.iterations == 2 && !mpdata::fused_tile_supported(o.dtype, grid, tx, ty))
+        return fail(MPDATA_EINVAL, "no fused kernel for tile %d x %d on this grid", tx, ty);
 
     mpdata_t *m = new (std::nothrow) mpdata_handle();
     if (!m) return fail(MPDATA_ENOMEM, "host allocation failed");
@@ -127,8 +130,7 @@ int mpdata_create(int nx, int ny, int nz, const mpdata_opts *opts, mpdata_t **ou
     m->nx = nx; m->ny = ny; m->nz = nz; m->n = n;
     m->opts = o;
     m->esize = o.dtype == MPDATA_F64 ? sizeof(double) : sizeof(float);
-    m->grid.nx = nx; m->grid.ny = ny; m->grid.nz = nz;
-    for (int d = 0; d < 3; ++d) m->grid.per[d] = o.periodic[d];
+    m->grid = grid;
     m->tile_x = tx; m->tile_y = ty;
     const size_t bytes = (size_t)n * m->esize;
     cudaError_t e = cudaMalloc(&m->scratch, bytes);

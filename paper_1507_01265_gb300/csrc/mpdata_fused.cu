@@ -404,20 +404,28 @@ cudaError_t launch_tile(const Grid &g, int nonosc, double eps, const void *h, co
 
 }  // namespace
 
-bool fused_tile_supported(int dtype, int tx, int ty) {
+static bool single_tile_supported(int dtype, int tx, int ty) {
     if (dtype == MPDATA_F64) return (tx == 16 && ty == 16);
     return (tx == 32 && ty == 16) || (tx == 24 && ty == 24) || (tx == 16 && ty == 16) ||
            (tx == 24 && ty == 16);
 }
 
-void fused_default_tile(int dtype, int *tx, int *ty) {
+bool fused_tile_supported(int dtype, const Grid &g, int tx, int ty) {
+    if (dtype == MPDATA_F32 && fused_pairs_supported(g, tx, ty)) return true;
+    return single_tile_supported(dtype, tx, ty);
+}
+
+void fused_default_tile(int dtype, const Grid &g, int *tx, int *ty) {
     if (dtype == MPDATA_F64) { *tx = 16; *ty = 16; }
+    else if (fused_pairs_supported(g, 32, 24)) { *tx = 32; *ty = 24; }
     else { *tx = 32; *ty = 16; }
 }
 
 cudaError_t launch_fused_step(int dtype, const Grid &g, int nonosc, double eps, int tx, int ty,
                               const void *h, const void *psi, const void *u1, const void *u2,
                               const void *u3, void *out, cudaStream_t s) {
+    if (dtype == MPDATA_F32 && fused_pairs_supported(g, tx, ty))
+        return launch_fused_pairs(g, nonosc, eps, tx, ty, h, psi, u1, u2, u3, out, s);
     if (dtype == MPDATA_F64) {
         if (tx == 16 && ty == 16)
             return launch_tile<double, 16, 16>(g, nonosc, eps, h, psi, u1, u2, u3, out, s);

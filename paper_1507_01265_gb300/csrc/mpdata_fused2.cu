@@ -1,0 +1,416 @@
+// Fused MPDATA step, FP32, two adjacent x-columns per thread.
+//
+// The same stage schedule as mpdata_fused.cu (a CTA marches a TX x TY tile
+// through z; per plane p: donor pass at p-1 | x/y pseudo-velocities at p-2 |
+// z-face pseudo-velocity and limiter factors at p-2 | limited corrective
+// fluxes at p-2 and the output of p-3), with three changes aimed at the
+// instruction count, which is what bounds this step on GB300:
+//   * each thread owns a pair of adjacent columns (i, i+1) and evaluates both
+//     with packed f32x2 add/mul/fma, so per-thread overhead (addressing,
+//     predicates, loop control) is paid once per two cells and shared-memory
+//     neighbours of the pair come in one 64-bit load;
+//   * inputs stream in as 16-byte cp.async chunks (this kernel requires nx to
+//     be a multiple of 4 so that chunks never straddle a wrap or a lid);
+//   * when x and y are both periodic (LID = false) every neighbour offset is
+//     a compile-time constant; with a lid on x or y (LID = true) the neighbour
+//     reads of cell fields are clamped (zero-gradient ghosts) and the lid
+//     faces are forced to zero velocity.
+// Threads are numbered from the tile outwards ring by ring in pair units, so
+// each stage's region is a prefix of the thread index.
+#include "mpdata_internal.cuh"
+
+namespace mpdata {
+namespace {
+
+using F2 = float2;
+
+__device__ __forceinline__ F2 bc(float a) { return make_float2(a, a); }
+__device__ __forceinline__ F2 add(F2 a, F2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ F2 mul(F2 a, F2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ F2 fma2(F2 a, F2 b, F2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ F2 sub(F2 a, F2 b) {
+    unsigned long long ra, rb, rc;
+    asm("mov.b64 %0, {%1,%2};" : "=l"(ra) : "f"(a.x), "f"(a.y));
+    asm("mov.b64 %0, {%1,%2};" : "=l"(rb) : "f"(b.x), "f"(b.y));
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(rc) : "l"(ra), "l"(rb));
+    F2 r;
+    asm("mov.b64 {%0,%1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(rc));
+    return r;
+}
+__device__ __forceinline__ float rcp1(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ F2 rcp(F2 a) { return make_float2(rcp1(a.x), rcp1(a.y)); }
+__device__ __forceinline__ F2 fabs2(F2 a) { return make_float2(fabsf(a.x), fabsf(a.y)); }
+__device__ __forceinline__ F2 pos(F2 a) { return make_float2(fmaxf(a.x, 0.f), fmaxf(a.y, 0.f)); }
+__device__ __forceinline__ F2 neg(F2 a) { return make_float2(fminf(a.x, 0.f), fminf(a.y, 0.f)); }
+__device__ __forceinline__ float max3f(float a, float b, float c) {
+    float r;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+__device__ __forceinline__ float min3f(float a, float b, float c) {
+    float r;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+__device__ __forceinline__ F2 max3(F2 a, F2 b, F2 c) {
+    return make_float2(max3f(a.x, b.x, c.x), max3f(a.y, b.y, c.y));
+}
+__device__ __forceinline__ F2 min3(F2 a, F2 b, F2 c) {
+    return make_float2(min3f(a.x, b.x, c.x), min3f(a.y, b.y, c.y));
+}
+// Upstream flux [U]+ L + [U]- R of each column of the pair.
+__device__ __forceinline__ F2 flux(F2 U, F2 L, F2 R) {
+    return mul(U, make_float2(U.x > 0.f ? L.x : R.x, U.y > 0.f ? L.y : R.y));
+}
+__device__ __forceinline__ F2 ld2(const float *p) { return *reinterpret_cast<const F2 *>(p); }
+__device__ __forceinline__ void st2(float *p, F2 v) { *reinterpret_cast<F2 *>(p) = v; }
+
+// Pseudo-velocity of both faces of the pair (see mpdata_fused.cu):
+//   V = (|U| - U^2/hbar) A - U (Ubar_a B_a + Ubar_b B_b) / hbar
+__device__ __forceinline__ F2 pseudo_velocity(F2 U, F2 pR, F2 pL, F2 spa, F2 sma, F2 ua, F2 spb,
+                                              F2 smb, F2 ub, F2 hsum, F2 eps) {
+    const F2 A = mul(sub(pR, pL), rcp(add(add(pR, pL), eps)));
+    const F2 Ba = mul(sub(spa, sma), rcp(add(add(spa, sma), eps)));
+    const F2 Bb = mul(sub(spb, smb), rcp(add(add(spb, smb), eps)));
+    const F2 r = mul(bc(2.f), rcp(hsum));                     // 1/hbar
+    const F2 cross = mul(bc(0.125f), fma2(ua, Ba, mul(ub, Bb)));  // 1/4 (Ubar) x 1/2 (B)
+    const F2 t = mul(U, r);
+    return sub(mul(sub(fabs2(U), mul(U, t)), A), mul(t, cross));
+}
+
+template <int TX, int TY>
+struct Lay2 {
+    static_assert(TX % 4 == 0, "TX must be a multiple of 4");
+    static constexpr int HX = TX / 2;           // output pairs per row
+    static constexpr int NPX = HX + 2;          // pairs of the radius-2 regions
+    static constexpr int EX = TX + 8;           // plane row: columns -4 .. TX+3
+    static constexpr int EY = TY + 6;           // plane rows: -3 .. TY+2
+    static constexpr int PL = EX * EY;
+    static constexpr int NT = NPX * (TY + 4);   // psi1 region = threads
+    static constexpr int N_OUT = HX * TY;
+    static constexpr int N_VM = (HX + 1) * (TY + 1);
+    static constexpr int N_BETA = NPX * (TY + 2);
+    static constexpr int N_V = NPX * (TY + 3);
+    static constexpr int CPR = EX / 4;          // 16-byte chunks per plane row
+    static constexpr int NCH = CPR * EY;
+    static_assert(NCH <= NT, "one load chunk per thread");
+    static constexpr int RING = 0, P1 = 20, SX = 22, SY = 24, SZ = 26;
+    static constexpr int V1 = 27, V2 = 28, BU = 29, BD = 30, GX = 31, GY = 32, NPLANES = 33;
+};
+
+// Pair (px, row) of thread t; pair px covers columns 2px-4, 2px-3 of the tile.
+// Rings outwards: out | col-pair HX+2 rows [0,TY], row TY | col-pair 1 rows
+// [-1,TY], row -1 | row TY+1 | row -2.
+template <int TX, int TY>
+__device__ __forceinline__ void onion2(int t, int &px, int &ry) {
+    using L = Lay2<TX, TY>;
+    constexpr int HX = L::HX;
+    if (t < L::N_OUT) { px = 2 + t % HX; ry = t / HX; return; }
+    t -= L::N_OUT;
+    if (t < TY + 1) { px = HX + 2; ry = t; return; }
+    t -= TY + 1;
+    if (t < HX) { px = 2 + t; ry = TY; return; }
+    t -= HX;
+    if (t < TY + 2) { px = 1; ry = t - 1; return; }
+    t -= TY + 2;
+    if (t < HX + 1) { px = 2 + t; ry = -1; return; }
+    t -= HX + 1;
+    if (t < HX + 2) { px = 1 + t; ry = TY + 1; return; }
+    t -= HX + 2;
+    px = 1 + t;
+    ry = -2;
+}
+
+__device__ __forceinline__ int wrap(int a, int n) {
+    a %= n;
+    return a < 0 ? a + n : a;
+}
+
+__device__ __forceinline__ void cp16(unsigned dst, const float *src, bool zero) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src),
+                 "r"(zero ? 0 : 16)
+                 : "memory");
+}
+
+template <int TX, int TY, bool NONOSC, bool LID>
+__global__ void __launch_bounds__(Lay2<TX, TY>::NT, 1)
+    k_fused_pairs(Grid g, float eps1, int ntx, const float *__restrict__ h,
+                  const float *__restrict__ psi, const float *__restrict__ u1,
+                  const float *__restrict__ u2, const float *__restrict__ u3,
+                  float *__restrict__ out) {
+    using L = Lay2<TX, TY>;
+    constexpr int EX = L::EX, PL = L::PL;
+    extern __shared__ __align__(16) float sm[];
+    const unsigned sm_base = (unsigned)__cvta_generic_to_shared(sm);
+#define PLANE(k) (sm + (k) * PL)
+#define RING(f, q) PLANE(L::RING + (f) * 4 + ((q) & 3))
+
+    const int t = threadIdx.x;
+    const int nx = g.nx, ny = g.ny, nz = g.nz;
+    const int perx = LID ? g.per[0] : 1, pery = LID ? g.per[1] : 1, perz = g.per[2];
+    const long long nxy = (long long)nx * ny;
+    const int x0 = (blockIdx.x % ntx) * TX, y0 = (blockIdx.x / ntx) * TY;
+    const F2 eps = bc(eps1);
+
+    int px, ry;
+    onion2<TX, TY>(t, px, ry);
+    const int gx = x0 + 2 * px - 4, gy = y0 + ry;  // global column of .x, row
+    const int c0 = (ry + 3) * EX + 2 * px;          // plane index of .x (even)
+    // lid handling (LID only): clamped neighbours and zero-velocity lid faces
+    const bool clampL = LID && !perx && gx == 0;
+    const bool clampR = LID && !perx && gx + 1 == nx - 1;
+    const int cD = c0 - ((LID && !pery && gy == 0) ? 0 : EX);
+    const int cU = c0 + ((LID && !pery && gy == ny - 1) ? 0 : EX);
+    const bool xlid0 = LID && !perx && (gx <= 0 || gx >= nx);
+    const bool xlid1 = LID && !perx && (gx + 1 <= 0 || gx + 1 >= nx);
+    const bool ylid = LID && !pery && (gy <= 0 || gy >= ny);
+    const bool in_vm = t < L::N_VM, in_beta = t < L::N_BETA, in_v = t < L::N_V,
+               in_out = t < L::N_OUT;
+    const bool store = in_out && gx < nx && gy < ny;
+    float *const outp = out + (long long)gy * nx + gx;
+
+    // pairs shifted by one column: (col-1, col) and (col+1, col+2)
+    auto lshC = [&](const float *P, F2 own) { return make_float2(clampL ? own.x : P[c0 - 1], own.x); };
+    auto rshC = [&](const float *P, F2 own) { return make_float2(own.y, clampR ? own.y : P[c0 + 2]); };
+    auto lshF = [&](const float *P, F2 own) { return make_float2(P[c0 - 1], own.x); };
+    auto rshF = [&](const float *P, F2 own) { return make_float2(own.y, P[c0 + 2]); };
+    auto lid2 = [&](F2 v, bool a, bool b) { return make_float2(a ? 0.f : v.x, b ? 0.f : v.y); };
+
+    // ---- this thread's 16-byte load chunk of the radius-3 plane ----
+    const bool has_chunk = t < L::NCH;
+    int ld_off = 0;
+    bool z_all = false, z_u2 = false, patch_u1 = false;
+    unsigned ld_dst = 0;
+    if (has_chunk) {
+        const int ey = t / L::CPR, cc = t % L::CPR;
+        const int lx = x0 - 4 + 4 * cc, ly = y0 - 3 + ey;
+        int cx, cy;
+        bool outx = false, outy = false;
+        if (perx) cx = wrap(lx, nx); else { outx = lx < 0 || lx >= nx; cx = outx ? 0 : lx; }
+        if (pery) cy = wrap(ly, ny); else { outy = ly < 0 || ly >= ny; cy = outy ? 0 : ly; }
+        z_all = outx || outy;                    // lid ghost: never read as a cell value
+        z_u2 = z_all || (!pery && ly == 0);      // y-lid face 0
+        patch_u1 = !perx && lx == 0;             // x-lid face 0 is this chunk's first element
+        ld_off = cy * nx + cx;
+        ld_dst = sm_base + (unsigned)(ey * EX + 4 * cc) * 4u;
+    }
+    auto issue = [&](int p) {
+        if (has_chunk) {
+            const long long pc = (long long)(perz ? wrap(p, nz) : min(max(p, 0), nz - 1)) * nxy + ld_off;
+            const bool zz = !perz && (p <= 0 || p >= nz);  // z-lid face
+            const unsigned d = ld_dst + (unsigned)((p & 3) * PL) * 4u;
+            constexpr unsigned fs = 4u * PL * 4u;  // bytes between fields
+            cp16(d, psi + pc, z_all);
+            cp16(d + fs, u1 + pc, z_all);
+            cp16(d + 2 * fs, u2 + pc, z_u2);
+            cp16(d + 3 * fs, u3 + pc, z_all || zz);
+            cp16(d + 4 * fs, h + pc, z_all);
+        }
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
+    };
+
+    const int p_first = perz ? -3 : -1;
+    const int p_last = nz + 2;
+    const int q1lo = perz ? -2 : 0, q1hi = perz ? nz + 1 : nz - 1;
+    const int q1top = perz ? q1hi : nz;
+    const int wlo = perz ? -2 : 0, whi = perz ? nz : nz - 2;
+    const int vlo = perz ? -1 : 0, vhi = perz ? nz : nz - 1;
+
+    const F2 Z = bc(0.f);
+    F2 pn_mm = Z, pn_m = Z, pn_c = Z;     // psi^n at q2-1, q2, q1
+    F2 p1a = Z, p1b = Z;                  // psi1 at q2-1, q2
+    F2 sxa = Z, sxb = Z, sya = Z, syb = Z;
+    F2 u1b = Z, u2b = Z, u3b = Z, hb = bc(1.f), u3c = Z;
+    F2 wlo_v = Z, bu_prev = Z, bd_prev = Z, h_prev = bc(1.f);
+    F2 dacc = Z, gx_own = Z, gy_own = Z;
+
+    issue(p_first);
+    for (int p = p_first; p <= p_last; ++p) {
+        const int q1 = p - 1, q2 = p - 2, q3 = p - 3;
+        if (p + 1 <= p_last) issue(p + 1);
+        else asm volatile("cp.async.commit_group;\n" ::: "memory");
+        asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+        if (LID && patch_u1 && has_chunk) RING(1, p)[(ld_dst - sm_base) / 4u] = 0.f;
+        __syncthreads();  // (A)
+
+        if (in_out && q3 >= 0 && q3 <= nz - 1) {
+            const F2 gxr = rshF(PLANE(L::GX), gx_own), gyu = ld2(PLANE(L::GY) + c0 + EX);
+            dacc = add(add(sub(gxr, gx_own), sub(gyu, gy_own)), dacc);
+        }
+
+        // (a1) donor pass at q1
+        const float *Pn = RING(0, q1);
+        const F2 pn_p = ld2(RING(0, p) + c0);
+        const F2 u3p = ld2(RING(3, p) + c0);
+        const float *U1c = RING(1, q1), *U2c = RING(2, q1);
+        const F2 u1c = ld2(U1c + c0), u2c = ld2(U2c + c0), hc = ld2(RING(4, q1) + c0);
+        F2 p1c = p1b;
+        if (q1 >= q1lo && q1 <= q1hi) {
+            const F2 fxl = flux(u1c, lshC(Pn, pn_c), pn_c);
+            const F2 fxh = flux(rshF(U1c, u1c), pn_c, rshC(Pn, pn_c));
+            const F2 fyl = flux(u2c, ld2(Pn + cD), pn_c);
+            const F2 fyh = flux(ld2(U2c + c0 + EX), pn_c, ld2(Pn + cU));
+            const F2 fzl = flux(u3c, pn_m, pn_c);
+            const F2 fzh = flux(u3p, pn_c, pn_p);
+            const F2 div = add(add(sub(fxh, fxl), sub(fyh, fyl)), sub(fzh, fzl));
+            p1c = sub(pn_c, mul(div, rcp(hc)));
+        }
+        if (q1 >= q1lo && q1 <= q1top) st2(PLANE(L::P1 + (q1 & 1)) + c0, p1c);
+        __syncthreads();  // (D)
+
+        // (a2) pair sums (all threads) and x/y pseudo-velocities at q2
+        const float *Pb = PLANE(L::P1 + (q2 & 1)), *Pc = PLANE(L::P1 + (q1 & 1));
+        F2 sxc = sxb, syc = syb, v1_own = Z, v2_own = Z, pl = Z, pd = Z;
+        if (q1 >= q1lo && q1 <= q1top) {
+            sxc = add(lshC(Pc, p1c), p1c);
+            syc = add(ld2(Pc + c0 - EX), p1c);
+            st2(PLANE(L::SX + (q1 & 1)) + c0, sxc);
+            st2(PLANE(L::SY + (q1 & 1)) + c0, syc);
+            st2(PLANE(L::SZ) + c0, add(p1b, p1c));
+        }
+        if (!perz && q1 == 0) { p1b = p1c; sxb = sxc; syb = syc; }
+        if (in_v && q2 >= vlo && q2 <= vhi) {
+            const float *U1b = RING(1, q2), *U2b = RING(2, q2), *U3b = RING(3, q2),
+                        *U3c = RING(3, q1), *Hb = RING(4, q2);
+            const float *Sxb = PLANE(L::SX + (q2 & 1)), *Syb = PLANE(L::SY + (q2 & 1));
+            pl = lshF(Pb, p1b);
+            pd = ld2(Pb + c0 - EX);
+            {   // x-faces: B_y from the x-pair sums above/below, B_z from the own queue
+                const F2 u2U = ld2(U2b + c0 + EX);
+                const F2 ua = add(add(add(lshF(U2b, u2b), u2b), make_float2(U2b[c0 + EX - 1], u2U.x)), u2U);
+                const F2 ub = add(add(add(lshF(U3b, u3b), u3b), lshF(U3c, u3c)), u3c);
+                const F2 v = pseudo_velocity(u1b, p1b, pl, ld2(Sxb + cU), ld2(Sxb + cD), ua, sxc, sxa,
+                                             ub, add(lshF(Hb, hb), hb), eps);
+                v1_own = LID ? lid2(v, xlid0, xlid1) : v;
+            }
+            {   // y-faces: B_z from the own queue, B_x from the y-pair sums left/right
+                const F2 u1D = ld2(U1b + c0 - EX);
+                const F2 va = add(add(add(ld2(U3b + c0 - EX), u3b), ld2(U3c + c0 - EX)), u3c);
+                const F2 vb = add(add(add(u1D, u1b), make_float2(u1D.y, U1b[c0 - EX + 2])), rshF(U1b, u1b));
+                const F2 v = pseudo_velocity(u2b, p1b, pd, syc, sya, va, rshC(Syb, syb), lshC(Syb, syb),
+                                             vb, add(ld2(Hb + c0 - EX), hb), eps);
+                v2_own = (LID && ylid) ? Z : v;
+            }
+            st2(PLANE(L::V1) + c0, v1_own);
+            st2(PLANE(L::V2) + c0, v2_own);
+        }
+        __syncthreads();  // (F)
+
+        // (a2) z-face above q2, (a3)+(a4) extrema and limiter factors at q2
+        F2 whi_v = Z, bu_c = Z, bd_c = Z;
+        if (in_beta) {
+            if (q2 >= wlo && q2 <= whi) {
+                const float *Sz = PLANE(L::SZ);
+                const F2 szo = add(p1b, p1c);
+                const F2 ua = add(add(add(u1b, u1c), rshF(RING(1, q2), u1b)), rshF(U1c, u1c));
+                const F2 ub = add(add(add(u2b, u2c), ld2(RING(2, q2) + c0 + EX)), ld2(U2c + c0 + EX));
+                whi_v = pseudo_velocity(u3c, p1c, p1b, rshC(Sz, szo), lshC(Sz, szo), ua, ld2(Sz + cU),
+                                        ld2(Sz + cD), ub, add(hb, hc), eps);
+            }
+            if (NONOSC && q2 >= vlo && q2 <= vhi) {
+                const float *Pnb = RING(0, q2);
+                const F2 aL = lshC(Pnb, pn_m), aR = rshC(Pnb, pn_m), aD = ld2(Pnb + cD), aU = ld2(Pnb + cU);
+                const F2 bL = lshC(Pb, p1b), bR = rshC(Pb, p1b), bD = ld2(Pb + cD), bU = ld2(Pb + cU);
+                F2 mx = max3(max3(aL, aR, aD), max3(aU, bL, bR), max3(bD, bU, pn_mm));
+                mx = max3(mx, max3(pn_m, pn_c, p1a), max3(p1b, p1c, p1b));
+                F2 mn = min3(min3(aL, aR, aD), min3(aU, bL, bR), min3(bD, bU, pn_mm));
+                mn = min3(mn, min3(pn_m, pn_c, p1a), min3(p1b, p1c, p1b));
+                const F2 v1h = rshF(PLANE(L::V1), v1_own), v2h = ld2(PLANE(L::V2) + c0 + EX);
+                const F2 in = add(add(sub(mul(pos(v1_own), bL), mul(neg(v1h), bR)),
+                                      sub(mul(pos(v2_own), bD), mul(neg(v2h), bU))),
+                                  sub(mul(pos(wlo_v), p1a), mul(neg(whi_v), p1c)));
+                const F2 outf = mul(add(add(sub(pos(v1h), neg(v1_own)), sub(pos(v2h), neg(v2_own))),
+                                        sub(pos(whi_v), neg(wlo_v))), p1b);
+                bu_c = mul(mul(sub(mx, p1b), hb), rcp(add(in, eps)));
+                bd_c = mul(mul(sub(p1b, mn), hb), rcp(add(outf, eps)));
+                st2(PLANE(L::BU) + c0, bu_c);
+                st2(PLANE(L::BD) + c0, bd_c);
+            }
+        }
+        __syncthreads();  // (H)
+
+        // (a5)+(a6) limited corrective fluxes at q2, output of q3
+        if (in_vm && q2 >= 0 && q2 <= nz - 1) {
+            F2 vm1 = v1_own, vm2 = v2_own;
+            if (NONOSC) {
+                const float *Bu = PLANE(L::BU), *Bd = PLANE(L::BD);
+                const F2 buL = lshF(Bu, bu_c), bdL = lshF(Bd, bd_c);
+                const F2 buD = ld2(Bu + c0 - EX), bdD = ld2(Bd + c0 - EX);
+                const F2 one = bc(1.f);
+                vm1 = add(mul(pos(v1_own), min3(one, bdL, bu_c)), mul(neg(v1_own), min3(one, buL, bd_c)));
+                vm2 = add(mul(pos(v2_own), min3(one, bdD, bu_c)), mul(neg(v2_own), min3(one, buD, bd_c)));
+            }
+            gx_own = flux(vm1, pl, p1b);
+            gy_own = flux(vm2, pd, p1b);
+            if (LID) {
+                gx_own = lid2(gx_own, xlid0, xlid1);
+                gy_own = ylid ? Z : gy_own;
+            }
+            st2(PLANE(L::GX) + c0, gx_own);
+            st2(PLANE(L::GY) + c0, gy_own);
+        }
+        const bool q3ok = q3 >= 0 && q3 <= nz - 1, q2ok = q2 >= 0 && q2 <= nz - 1;
+        if (in_out && (q3ok || q2ok)) {
+            F2 gz = Z;
+            if (perz || (q2 >= 1 && q2 <= nz - 1)) {
+                F2 vm3 = wlo_v;
+                if (NONOSC) {
+                    const F2 one = bc(1.f);
+                    vm3 = add(mul(pos(wlo_v), min3(one, bd_prev, bu_c)), mul(neg(wlo_v), min3(one, bu_prev, bd_c)));
+                }
+                gz = flux(vm3, p1a, p1b);
+            }
+            if (q3ok && store) st2(outp + (long long)q3 * nxy, sub(p1a, mul(add(dacc, gz), rcp(h_prev))));
+            dacc = sub(Z, gz);
+        }
+
+        h_prev = hb;
+        pn_mm = pn_m; pn_m = pn_c; pn_c = pn_p;
+        p1a = p1b; p1b = p1c;
+        sxa = sxb; sxb = sxc; sya = syb; syb = syc;
+        u1b = u1c; u2b = u2c; u3b = u3c; u3c = u3p; hb = hc;
+        wlo_v = whi_v; bu_prev = bu_c; bd_prev = bd_c;
+    }
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
+#undef RING
+#undef PLANE
+}
+
+template <int TX, int TY>
+cudaError_t launch_pairs(const Grid &g, int nonosc, double eps, const void *h, const void *psi,
+                         const void *u1, const void *u2, const void *u3, void *out, cudaStream_t s) {
+    using L = Lay2<TX, TY>;
+    const size_t smem = (size_t)L::NPLANES * L::PL * sizeof(float);
+    const int ntx = (g.nx + TX - 1) / TX, nty = (g.ny + TY - 1) / TY;
+    const bool lid = !g.per[0] || !g.per[1];
+    auto kern = nonosc ? (lid ? k_fused_pairs<TX, TY, true, true> : k_fused_pairs<TX, TY, true, false>)
+                       : (lid ? k_fused_pairs<TX, TY, false, true> : k_fused_pairs<TX, TY, false, false>);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<ntx * nty, L::NT, smem, s>>>(g, (float)eps, ntx, (const float *)h, (const float *)psi,
+                                        (const float *)u1, (const float *)u2, (const float *)u3,
+                                        (float *)out);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+bool fused_pairs_supported(const Grid &g, int tx, int ty) {
+    if (g.nx % 4 != 0) return false;
+    return tx == 32 && (ty == 16 || ty == 24);
+}
+
+cudaError_t launch_fused_pairs(const Grid &g, int nonosc, double eps, int tx, int ty, const void *h,
+                               const void *psi, const void *u1, const void *u2, const void *u3,
+                               void *out, cudaStream_t s) {
+    if (g.nx % 4 != 0) return cudaErrorInvalidValue;
+    if (tx == 32 && ty == 16) return launch_pairs<32, 16>(g, nonosc, eps, h, psi, u1, u2, u3, out, s);
+    if (tx == 32 && ty == 24) return launch_pairs<32, 24>(g, nonosc, eps, h, psi, u1, u2, u3, out, s);
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace mpdata

@@ -41,13 +41,19 @@ cudaError_t launch_stage_step(int dtype, const Grid &g, int iterations, int nono
                               const void *h, const void *psi, const void *u1, const void *u2,
                               const void *u3, void *out, const StageBuffers &b, cudaStream_t s);
 
-// Fused step (mpdata_fused.cu).  Returns cudaErrorInvalidValue for a tile
-// shape that has no compiled instance.
+// Fused step.  FP32 grids with nx % 4 == 0 and a pair tile (32x16, 32x24)
+// run the two-columns-per-thread kernel (mpdata_fused2.cu); everything else
+// runs the one-column kernel (mpdata_fused.cu).  Returns
+// cudaErrorInvalidValue for a tile shape with no compiled instance.
 cudaError_t launch_fused_step(int dtype, const Grid &g, int nonosc, double eps, int tile_x,
                               int tile_y, const void *h, const void *psi, const void *u1,
                               const void *u2, const void *u3, void *out, cudaStream_t s);
-bool fused_tile_supported(int dtype, int tile_x, int tile_y);
-void fused_default_tile(int dtype, int *tile_x, int *tile_y);
+bool fused_tile_supported(int dtype, const Grid &g, int tile_x, int tile_y);
+void fused_default_tile(int dtype, const Grid &g, int *tile_x, int *tile_y);
+bool fused_pairs_supported(const Grid &g, int tile_x, int tile_y);
+cudaError_t launch_fused_pairs(const Grid &g, int nonosc, double eps, int tile_x, int tile_y,
+                               const void *h, const void *psi, const void *u1, const void *u2,
+                               const void *u3, void *out, cudaStream_t s);
 
 // Deterministic FP64 diagnostics (mpdata_reduce.cu).
 constexpr int kReduceBlocks = 1024;  // fixed, so the summation tree never changes
