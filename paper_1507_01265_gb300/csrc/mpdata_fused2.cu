@@ -136,6 +136,26 @@ __device__ __forceinline__ void cp16(unsigned dst, const float *src, bool zero) 
                  : "memory");
 }
 
+// Shared-memory access with explicit 32-bit addresses: one per-thread base
+// plus per-iteration slot bases; every field, plane and neighbour offset is a
+// compile-time immediate of the load/store.
+template <int OFF>
+__device__ __forceinline__ F2 ldp(unsigned b) {
+    F2 v;
+    asm volatile("ld.shared.v2.f32 {%0,%1}, [%2+%3];" : "=f"(v.x), "=f"(v.y) : "r"(b), "n"(OFF));
+    return v;
+}
+template <int OFF>
+__device__ __forceinline__ float lds(unsigned b) {
+    float v;
+    asm volatile("ld.shared.f32 %0, [%1+%2];" : "=f"(v) : "r"(b), "n"(OFF));
+    return v;
+}
+template <int OFF>
+__device__ __forceinline__ void stp(unsigned b, F2 v) {
+    asm volatile("st.shared.v2.f32 [%0+%1], {%2,%3};" ::"r"(b), "n"(OFF), "f"(v.x), "f"(v.y) : "memory");
+}
+
 template <int TX, int TY, bool NONOSC, bool LID>
 __global__ void __launch_bounds__(Lay2<TX, TY>::NT, 1)
     k_fused_pairs(Grid g, float eps1, int ntx, const float *__restrict__ h,
@@ -144,10 +164,15 @@ __global__ void __launch_bounds__(Lay2<TX, TY>::NT, 1)
                   float *__restrict__ out) {
     using L = Lay2<TX, TY>;
     constexpr int EX = L::EX, PL = L::PL;
+    constexpr int PB = PL * 4;         // bytes per plane
+    constexpr int FB = 4 * PB;         // bytes between ring fields
+    constexpr int RB = EX * 4;         // bytes per plane row
+    // plane offsets (bytes) of the non-ring planes
+    constexpr int oP1 = L::P1 * PB, oSX = L::SX * PB, oSY = L::SY * PB, oSZ = L::SZ * PB;
+    constexpr int oV1 = L::V1 * PB, oV2 = L::V2 * PB, oBU = L::BU * PB, oBD = L::BD * PB;
+    constexpr int oGX = L::GX * PB, oGY = L::GY * PB;
     extern __shared__ __align__(16) float sm[];
     const unsigned sm_base = (unsigned)__cvta_generic_to_shared(sm);
-#define PLANE(k) (sm + (k) * PL)
-#define RING(f, q) PLANE(L::RING + (f) * 4 + ((q) & 3))
 
     const int t = threadIdx.x;
     const int nx = g.nx, ny = g.ny, nz = g.nz;
@@ -159,12 +184,12 @@ __global__ void __launch_bounds__(Lay2<TX, TY>::NT, 1)
     int px, ry;
     onion2<TX, TY>(t, px, ry);
     const int gx = x0 + 2 * px - 4, gy = y0 + ry;  // global column of .x, row
-    const int c0 = (ry + 3) * EX + 2 * px;          // plane index of .x (even)
-    // lid handling (LID only): clamped neighbours and zero-velocity lid faces
+    const unsigned tb = sm_base + (unsigned)((ry + 3) * EX + 2 * px) * 4u;
+    // lid handling (LID only): clamped neighbours, zero-velocity lid faces
     const bool clampL = LID && !perx && gx == 0;
     const bool clampR = LID && !perx && gx + 1 == nx - 1;
-    const int cD = c0 - ((LID && !pery && gy == 0) ? 0 : EX);
-    const int cU = c0 + ((LID && !pery && gy == ny - 1) ? 0 : EX);
+    const int dD = (LID && !pery && gy == 0) ? 0 : -RB;       // clamped row below (bytes)
+    const int dU = (LID && !pery && gy == ny - 1) ? 0 : RB;   // clamped row above
     const bool xlid0 = LID && !perx && (gx <= 0 || gx >= nx);
     const bool xlid1 = LID && !perx && (gx + 1 <= 0 || gx + 1 >= nx);
     const bool ylid = LID && !pery && (gy <= 0 || gy >= ny);
@@ -173,12 +198,16 @@ __global__ void __launch_bounds__(Lay2<TX, TY>::NT, 1)
     const bool store = in_out && gx < nx && gy < ny;
     float *const outp = out + (long long)gy * nx + gx;
 
-    // pairs shifted by one column: (col-1, col) and (col+1, col+2)
-    auto lshC = [&](const float *P, F2 own) { return make_float2(clampL ? own.x : P[c0 - 1], own.x); };
-    auto rshC = [&](const float *P, F2 own) { return make_float2(own.y, clampR ? own.y : P[c0 + 2]); };
-    auto lshF = [&](const float *P, F2 own) { return make_float2(P[c0 - 1], own.x); };
-    auto rshF = [&](const float *P, F2 own) { return make_float2(own.y, P[c0 + 2]); };
-    auto lid2 = [&](F2 v, bool a, bool b) { return make_float2(a ? 0.f : v.x, b ? 0.f : v.y); };
+    // cell-field pairs one row down/up (clamped on a y-lid)
+    auto ldD = [&](unsigned b) { if constexpr (LID) return ldp<0>(b + dD); else return ldp<-RB>(b); };
+    auto ldU = [&](unsigned b) { if constexpr (LID) return ldp<0>(b + dU); else return ldp<RB>(b); };
+    // pairs shifted by one column, (col-1, col) and (col+1, col+2): cell
+    // fields clamp on an x-lid, face fields do not
+    auto lshC = [&](unsigned b, F2 own) { float a = lds<-4>(b); return make_float2(clampL ? own.x : a, own.x); };
+    auto rshC = [&](unsigned b, F2 own) { float a = lds<8>(b); return make_float2(own.y, clampR ? own.y : a); };
+    auto lshF = [&](unsigned b, F2 own) { return make_float2(lds<-4>(b), own.x); };
+    auto rshF = [&](unsigned b, F2 own) { return make_float2(own.y, lds<8>(b)); };
+    auto lid2 = [&](F2 v, bool a, bool c) { return make_float2(a ? 0.f : v.x, c ? 0.f : v.y); };
 
     // ---- this thread's 16-byte load chunk of the radius-3 plane ----
     const bool has_chunk = t < L::NCH;
@@ -194,7 +223,7 @@ __global__ void __launch_bounds__(Lay2<TX, TY>::NT, 1)
         if (pery) cy = wrap(ly, ny); else { outy = ly < 0 || ly >= ny; cy = outy ? 0 : ly; }
         z_all = outx || outy;                    // lid ghost: never read as a cell value
         z_u2 = z_all || (!pery && ly == 0);      // y-lid face 0
-        patch_u1 = !perx && lx == 0;             // x-lid face 0 is this chunk's first element
+        patch_u1 = LID && !perx && lx == 0;      // x-lid face 0 is this chunk's first element
         ld_off = cy * nx + cx;
         ld_dst = sm_base + (unsigned)(ey * EX + 4 * cc) * 4u;
     }
@@ -202,13 +231,12 @@ __global__ void __launch_bounds__(Lay2<TX, TY>::NT, 1)
         if (has_chunk) {
             const long long pc = (long long)(perz ? wrap(p, nz) : min(max(p, 0), nz - 1)) * nxy + ld_off;
             const bool zz = !perz && (p <= 0 || p >= nz);  // z-lid face
-            const unsigned d = ld_dst + (unsigned)((p & 3) * PL) * 4u;
-            constexpr unsigned fs = 4u * PL * 4u;  // bytes between fields
+            const unsigned d = ld_dst + (unsigned)((p & 3) * PB);
             cp16(d, psi + pc, z_all);
-            cp16(d + fs, u1 + pc, z_all);
-            cp16(d + 2 * fs, u2 + pc, z_u2);
-            cp16(d + 3 * fs, u3 + pc, z_all || zz);
-            cp16(d + 4 * fs, h + pc, z_all);
+            cp16(d + FB, u1 + pc, z_all);
+            cp16(d + 2 * FB, u2 + pc, z_u2);
+            cp16(d + 3 * FB, u3 + pc, z_all || zz);
+            cp16(d + 4 * FB, h + pc, z_all);
         }
         asm volatile("cp.async.commit_group;\n" ::: "memory");
     };
@@ -234,69 +262,72 @@ __global__ void __launch_bounds__(Lay2<TX, TY>::NT, 1)
         if (p + 1 <= p_last) issue(p + 1);
         else asm volatile("cp.async.commit_group;\n" ::: "memory");
         asm volatile("cp.async.wait_group 1;\n" ::: "memory");
-        if (LID && patch_u1 && has_chunk) RING(1, p)[(ld_dst - sm_base) / 4u] = 0.f;
+        if (LID && patch_u1) sm[(ld_dst - sm_base) / 4u + (unsigned)(L::RING * PL + 4 * PL + (p & 3) * PL)] = 0.f;
         __syncthreads();  // (A)
 
+        // slot bases of this iteration
+        const unsigned rp = tb + (unsigned)((p & 3) * PB);    // ring, plane p
+        const unsigned r1 = tb + (unsigned)((q1 & 3) * PB);   // ring, plane q1
+        const unsigned r2 = tb + (unsigned)((q2 & 3) * PB);   // ring, plane q2
+        const unsigned b1 = tb + (unsigned)((q1 & 1) * PB);   // psi1/SX/SY slot of q1
+        const unsigned b2 = tb + (unsigned)((q2 & 1) * PB);   // psi1/SX/SY slot of q2
+
         if (in_out && q3 >= 0 && q3 <= nz - 1) {
-            const F2 gxr = rshF(PLANE(L::GX), gx_own), gyu = ld2(PLANE(L::GY) + c0 + EX);
+            const F2 gxr = rshF(tb + oGX, gx_own), gyu = ldp<oGY + RB>(tb);
             dacc = add(add(sub(gxr, gx_own), sub(gyu, gy_own)), dacc);
         }
 
         // (a1) donor pass at q1
-        const float *Pn = RING(0, q1);
-        const F2 pn_p = ld2(RING(0, p) + c0);
-        const F2 u3p = ld2(RING(3, p) + c0);
-        const float *U1c = RING(1, q1), *U2c = RING(2, q1);
-        const F2 u1c = ld2(U1c + c0), u2c = ld2(U2c + c0), hc = ld2(RING(4, q1) + c0);
+        const F2 pn_p = ldp<0>(rp);
+        const F2 u3p = ldp<3 * FB>(rp);
+        const F2 u1c = ldp<FB>(r1), u2c = ldp<2 * FB>(r1), hc = ldp<4 * FB>(r1);
         F2 p1c = p1b;
         if (q1 >= q1lo && q1 <= q1hi) {
-            const F2 fxl = flux(u1c, lshC(Pn, pn_c), pn_c);
-            const F2 fxh = flux(rshF(U1c, u1c), pn_c, rshC(Pn, pn_c));
-            const F2 fyl = flux(u2c, ld2(Pn + cD), pn_c);
-            const F2 fyh = flux(ld2(U2c + c0 + EX), pn_c, ld2(Pn + cU));
+            const F2 fxl = flux(u1c, lshC(r1, pn_c), pn_c);
+            const F2 fxh = flux(rshF(r1 + FB, u1c), pn_c, rshC(r1, pn_c));
+            const F2 fyl = flux(u2c, ldD(r1), pn_c);
+            const F2 fyh = flux(ldp<2 * FB + RB>(r1), pn_c, ldU(r1));
             const F2 fzl = flux(u3c, pn_m, pn_c);
             const F2 fzh = flux(u3p, pn_c, pn_p);
             const F2 div = add(add(sub(fxh, fxl), sub(fyh, fyl)), sub(fzh, fzl));
             p1c = sub(pn_c, mul(div, rcp(hc)));
         }
-        if (q1 >= q1lo && q1 <= q1top) st2(PLANE(L::P1 + (q1 & 1)) + c0, p1c);
+        if (q1 >= q1lo && q1 <= q1top) stp<oP1>(b1, p1c);
         __syncthreads();  // (D)
 
         // (a2) pair sums (all threads) and x/y pseudo-velocities at q2
-        const float *Pb = PLANE(L::P1 + (q2 & 1)), *Pc = PLANE(L::P1 + (q1 & 1));
         F2 sxc = sxb, syc = syb, v1_own = Z, v2_own = Z, pl = Z, pd = Z;
         if (q1 >= q1lo && q1 <= q1top) {
-            sxc = add(lshC(Pc, p1c), p1c);
-            syc = add(ld2(Pc + c0 - EX), p1c);
-            st2(PLANE(L::SX + (q1 & 1)) + c0, sxc);
-            st2(PLANE(L::SY + (q1 & 1)) + c0, syc);
-            st2(PLANE(L::SZ) + c0, add(p1b, p1c));
+            sxc = add(lshC(b1 + oP1, p1c), p1c);
+            syc = add(ldp<oP1 - RB>(b1), p1c);
+            stp<oSX>(b1, sxc);
+            stp<oSY>(b1, syc);
+            stp<oSZ>(tb, add(p1b, p1c));
         }
         if (!perz && q1 == 0) { p1b = p1c; sxb = sxc; syb = syc; }
         if (in_v && q2 >= vlo && q2 <= vhi) {
-            const float *U1b = RING(1, q2), *U2b = RING(2, q2), *U3b = RING(3, q2),
-                        *U3c = RING(3, q1), *Hb = RING(4, q2);
-            const float *Sxb = PLANE(L::SX + (q2 & 1)), *Syb = PLANE(L::SY + (q2 & 1));
-            pl = lshF(Pb, p1b);
-            pd = ld2(Pb + c0 - EX);
+            pl = lshF(b2 + oP1, p1b);
+            pd = ldp<oP1 - RB>(b2);
             {   // x-faces: B_y from the x-pair sums above/below, B_z from the own queue
-                const F2 u2U = ld2(U2b + c0 + EX);
-                const F2 ua = add(add(add(lshF(U2b, u2b), u2b), make_float2(U2b[c0 + EX - 1], u2U.x)), u2U);
-                const F2 ub = add(add(add(lshF(U3b, u3b), u3b), lshF(U3c, u3c)), u3c);
-                const F2 v = pseudo_velocity(u1b, p1b, pl, ld2(Sxb + cU), ld2(Sxb + cD), ua, sxc, sxa,
-                                             ub, add(lshF(Hb, hb), hb), eps);
+                const F2 u2U = ldp<2 * FB + RB>(r2);
+                const F2 ua = add(add(add(lshF(r2 + 2 * FB, u2b), u2b),
+                                      make_float2(lds<2 * FB + RB - 4>(r2), u2U.x)), u2U);
+                const F2 ub = add(add(add(lshF(r2 + 3 * FB, u3b), u3b), lshF(r1 + 3 * FB, u3c)), u3c);
+                const F2 v = pseudo_velocity(u1b, p1b, pl, ldU(b2 + oSX), ldD(b2 + oSX), ua, sxc, sxa,
+                                             ub, add(lshF(r2 + 4 * FB, hb), hb), eps);
                 v1_own = LID ? lid2(v, xlid0, xlid1) : v;
             }
             {   // y-faces: B_z from the own queue, B_x from the y-pair sums left/right
-                const F2 u1D = ld2(U1b + c0 - EX);
-                const F2 va = add(add(add(ld2(U3b + c0 - EX), u3b), ld2(U3c + c0 - EX)), u3c);
-                const F2 vb = add(add(add(u1D, u1b), make_float2(u1D.y, U1b[c0 - EX + 2])), rshF(U1b, u1b));
-                const F2 v = pseudo_velocity(u2b, p1b, pd, syc, sya, va, rshC(Syb, syb), lshC(Syb, syb),
-                                             vb, add(ld2(Hb + c0 - EX), hb), eps);
+                const F2 u1D = ldp<FB - RB>(r2);
+                const F2 va = add(add(add(ldp<3 * FB - RB>(r2), u3b), ldp<3 * FB - RB>(r1)), u3c);
+                const F2 vb = add(add(add(u1D, u1b), make_float2(u1D.y, lds<FB - RB + 8>(r2))),
+                                  rshF(r2 + FB, u1b));
+                const F2 v = pseudo_velocity(u2b, p1b, pd, syc, sya, va, rshC(b2 + oSY, syb),
+                                             lshC(b2 + oSY, syb), vb, add(ldp<4 * FB - RB>(r2), hb), eps);
                 v2_own = (LID && ylid) ? Z : v;
             }
-            st2(PLANE(L::V1) + c0, v1_own);
-            st2(PLANE(L::V2) + c0, v2_own);
+            stp<oV1>(tb, v1_own);
+            stp<oV2>(tb, v2_own);
         }
         __syncthreads();  // (F)
 
@@ -304,22 +335,21 @@ __global__ void __launch_bounds__(Lay2<TX, TY>::NT, 1)
         F2 whi_v = Z, bu_c = Z, bd_c = Z;
         if (in_beta) {
             if (q2 >= wlo && q2 <= whi) {
-                const float *Sz = PLANE(L::SZ);
                 const F2 szo = add(p1b, p1c);
-                const F2 ua = add(add(add(u1b, u1c), rshF(RING(1, q2), u1b)), rshF(U1c, u1c));
-                const F2 ub = add(add(add(u2b, u2c), ld2(RING(2, q2) + c0 + EX)), ld2(U2c + c0 + EX));
-                whi_v = pseudo_velocity(u3c, p1c, p1b, rshC(Sz, szo), lshC(Sz, szo), ua, ld2(Sz + cU),
-                                        ld2(Sz + cD), ub, add(hb, hc), eps);
+                const F2 ua = add(add(add(u1b, u1c), rshF(r2 + FB, u1b)), rshF(r1 + FB, u1c));
+                const F2 ub = add(add(add(u2b, u2c), ldp<2 * FB + RB>(r2)), ldp<2 * FB + RB>(r1));
+                whi_v = pseudo_velocity(u3c, p1c, p1b, rshC(tb + oSZ, szo), lshC(tb + oSZ, szo), ua,
+                                        ldU(tb + oSZ), ldD(tb + oSZ), ub, add(hb, hc), eps);
             }
             if (NONOSC && q2 >= vlo && q2 <= vhi) {
-                const float *Pnb = RING(0, q2);
-                const F2 aL = lshC(Pnb, pn_m), aR = rshC(Pnb, pn_m), aD = ld2(Pnb + cD), aU = ld2(Pnb + cU);
-                const F2 bL = lshC(Pb, p1b), bR = rshC(Pb, p1b), bD = ld2(Pb + cD), bU = ld2(Pb + cU);
+                const F2 aL = lshC(r2, pn_m), aR = rshC(r2, pn_m), aD = ldD(r2), aU = ldU(r2);
+                const F2 bL = lshC(b2 + oP1, p1b), bR = rshC(b2 + oP1, p1b);
+                const F2 bD = ldD(b2 + oP1), bU = ldU(b2 + oP1);
                 F2 mx = max3(max3(aL, aR, aD), max3(aU, bL, bR), max3(bD, bU, pn_mm));
                 mx = max3(mx, max3(pn_m, pn_c, p1a), max3(p1b, p1c, p1b));
                 F2 mn = min3(min3(aL, aR, aD), min3(aU, bL, bR), min3(bD, bU, pn_mm));
                 mn = min3(mn, min3(pn_m, pn_c, p1a), min3(p1b, p1c, p1b));
-                const F2 v1h = rshF(PLANE(L::V1), v1_own), v2h = ld2(PLANE(L::V2) + c0 + EX);
+                const F2 v1h = rshF(tb + oV1, v1_own), v2h = ldp<oV2 + RB>(tb);
                 const F2 in = add(add(sub(mul(pos(v1_own), bL), mul(neg(v1h), bR)),
                                       sub(mul(pos(v2_own), bD), mul(neg(v2h), bU))),
                                   sub(mul(pos(wlo_v), p1a), mul(neg(whi_v), p1c)));
@@ -327,8 +357,8 @@ __global__ void __launch_bounds__(Lay2<TX, TY>::NT, 1)
                                         sub(pos(whi_v), neg(wlo_v))), p1b);
                 bu_c = mul(mul(sub(mx, p1b), hb), rcp(add(in, eps)));
                 bd_c = mul(mul(sub(p1b, mn), hb), rcp(add(outf, eps)));
-                st2(PLANE(L::BU) + c0, bu_c);
-                st2(PLANE(L::BD) + c0, bd_c);
+                stp<oBU>(tb, bu_c);
+                stp<oBD>(tb, bd_c);
             }
         }
         __syncthreads();  // (H)
@@ -337,9 +367,8 @@ __global__ void __launch_bounds__(Lay2<TX, TY>::NT, 1)
         if (in_vm && q2 >= 0 && q2 <= nz - 1) {
             F2 vm1 = v1_own, vm2 = v2_own;
             if (NONOSC) {
-                const float *Bu = PLANE(L::BU), *Bd = PLANE(L::BD);
-                const F2 buL = lshF(Bu, bu_c), bdL = lshF(Bd, bd_c);
-                const F2 buD = ld2(Bu + c0 - EX), bdD = ld2(Bd + c0 - EX);
+                const F2 buL = lshF(tb + oBU, bu_c), bdL = lshF(tb + oBD, bd_c);
+                const F2 buD = ldp<oBU - RB>(tb), bdD = ldp<oBD - RB>(tb);
                 const F2 one = bc(1.f);
                 vm1 = add(mul(pos(v1_own), min3(one, bdL, bu_c)), mul(neg(v1_own), min3(one, buL, bd_c)));
                 vm2 = add(mul(pos(v2_own), min3(one, bdD, bu_c)), mul(neg(v2_own), min3(one, buD, bd_c)));
@@ -350,8 +379,8 @@ __global__ void __launch_bounds__(Lay2<TX, TY>::NT, 1)
                 gx_own = lid2(gx_own, xlid0, xlid1);
                 gy_own = ylid ? Z : gy_own;
             }
-            st2(PLANE(L::GX) + c0, gx_own);
-            st2(PLANE(L::GY) + c0, gy_own);
+            stp<oGX>(tb, gx_own);
+            stp<oGY>(tb, gy_own);
         }
         const bool q3ok = q3 >= 0 && q3 <= nz - 1, q2ok = q2 >= 0 && q2 <= nz - 1;
         if (in_out && (q3ok || q2ok)) {
@@ -376,8 +405,6 @@ __global__ void __launch_bounds__(Lay2<TX, TY>::NT, 1)
         wlo_v = whi_v; bu_prev = bu_c; bd_prev = bd_c;
     }
     asm volatile("cp.async.wait_all;\n" ::: "memory");
-#undef RING
-#undef PLANE
 }
 
 template <int TX, int TY>
