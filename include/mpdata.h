@@ -135,6 +135,137 @@ int mpdata_mass(mpdata_t *handle, const void *h, const void *psi, void *out3, vo
 int mpdata_mass_noalloc(const void *h, const void *psi, long long n, int dtype, void *out3,
                         void *stream);
 
+/* ---- batches: many independent grids advanced by persistent launches ----
+ *
+ * The paper's team decomposition (§5.3) assigns sub-domains to groups of
+ * cores; here every grid of the batch is cut into the same tiles as a
+ * single-grid launch, the tiles of all grids form a work-item list, and a
+ * persistent launch of one CTA per SM runs the list with CTA c taking the
+ * contiguous items [begin[c], begin[c+1]).  The default split balances the
+ * estimated cost (tile area x (nz + 3)); mpdata_batch_set_split installs any
+ * other, e.g. the uneven splits of the speed-function partitioner
+ * (Algorithm 1, §4).  Grids with nx % 4 == 0 use the two-column kernel
+ * (variant 0: x and y periodic, variant 1: a lid on x or y), others the
+ * one-column kernel (variant 2).  FP32, iterations = 2 only.  Each grid's
+ * result is bit-identical to mpdata_step on that grid alone. */
+typedef struct mpdata_batch mpdata_batch_t;
+
+/* dims: 3*ngrids ints (nx, ny, nz of each grid); periodic: 3*ngrids flags or
+ * NULL for opts->periodic on every grid; opts: NULL for defaults (dtype must
+ * be MPDATA_F32; tile 32x24 (default) or 32x16).  Allocates one psi-sized
+ * scratch buffer per grid.  Errors: EINVAL, ENOMEM, ECUDA. */
+int mpdata_batch_create(int ngrids, const int *dims, const int *periodic, const mpdata_opts *opts,
+                        mpdata_batch_t **out);
+/* Device pointers (16-byte aligned) of grid `grid`; psi is advanced in
+ * place.  Must be set for every grid before the first step. */
+int mpdata_batch_set_fields(mpdata_batch_t *batch, int grid, const void *h, void *psi,
+                            const void *u1, const void *u2, const void *u3);
+/* Number of work items and CTAs of a variant (0, 1, 2). */
+int mpdata_batch_work(mpdata_batch_t *batch, int variant, int *nitems, int *ncta);
+/* Copy the current split of a variant (ncta + 1 ints) into begin. */
+int mpdata_batch_get_split(mpdata_batch_t *batch, int variant, int *begin);
+/* Install a split: ncta CTAs, begin[0] = 0, begin[ncta] = nitems,
+ * nondecreasing (a CTA may get no item). */
+int mpdata_batch_set_split(mpdata_batch_t *batch, int variant, int ncta, const int *begin);
+/* nsteps steps of every grid (async on stream).  use_graph != 0 captures the
+ * whole sequence once per nsteps into a CUDA graph and replays it (the graph
+ * is rebuilt after set_fields or set_split).  Odd nsteps copies each psi to
+ * its scratch first so that the result lands in psi. */
+int mpdata_batch_step(mpdata_batch_t *batch, int nsteps, int use_graph, void *stream);
+int mpdata_batch_destroy(mpdata_batch_t *batch);
+
+/* ---- serving: continuous batching of advection solves ----
+ *
+ * A server owns a scheduler thread and a CUDA stream on the device current at
+ * creation.  Requests (host fields, FP32) are admitted first-in first-out
+ * while their device footprint (6 fields: h, psi, psi scratch, u1, u2, u3)
+ * fits the HBM budget and fewer than max_active are resident; every tick
+ * advances all resident requests by the same chunk of steps in one persistent
+ * batched launch per kernel variant (see mpdata_batch_*), so requests that
+ * arrive while others run join at the next tick and share the GPU.  A
+ * finished request's psi is copied back into its host buffer, then its
+ * memory and budget are released.  Each result is bit-identical to
+ * mpdata_step on that grid alone.  Host buffers must stay valid until the
+ * request finishes; pinned memory keeps the scheduler from blocking on
+ * copies.  All entry points are thread-safe. */
+#define MPDATA_REQ_QUEUED 0    /* waiting for budget or a slot */
+#define MPDATA_REQ_RUNNING 1   /* resident on the device */
+#define MPDATA_REQ_DONE 2      /* psi holds the result */
+#define MPDATA_REQ_FAILED 3    /* see mpdata_wait's return code */
+#define MPDATA_REQ_CANCELLED 4
+
+typedef struct mpdata_server_opts {
+    uint32_t size;              /* sizeof(mpdata_server_opts) */
+    size_t hbm_budget_bytes;    /* device memory the server may hold (default 8 GiB) */
+    int32_t max_active;         /* resident requests at most (default 256) */
+    int32_t max_queued;         /* requests waiting for memory; a submit beyond this that
+                                   cannot be covered by the budget gets EBUSY (default 2^20;
+                                   0 = reserve budget at submit, refuse when over) */
+    int32_t chunk_steps;        /* steps per tick (default 8) */
+    int32_t tile_y;             /* 24 (default) or 16 for the two-column kernel */
+    int32_t nonoscillatory;     /* default 1 */
+    int32_t inject_alloc_failure; /* test hook: every n-th admission fails as out of memory (0 = off) */
+    double eps;                 /* default 1e-15 */
+} mpdata_server_opts;
+
+typedef struct mpdata_request {
+    uint32_t size;              /* sizeof(mpdata_request) */
+    int32_t nx, ny, nz;
+    int32_t periodic[3];
+    int32_t nsteps;             /* >= 0 */
+    const void *h, *u1, *u2, *u3; /* host float32 [nz][ny][nx] */
+    void *psi;                  /* host float32: initial state in, result out */
+} mpdata_request;
+
+typedef struct mpdata_server mpdata_server_t;
+
+void mpdata_server_opts_default(mpdata_server_opts *opts);
+/* Errors: EINVAL (options), ENOMEM, ECUDA. */
+int mpdata_server_create(const mpdata_server_opts *opts, mpdata_server_t **out);
+/* Queue a request; *ticket identifies it.  Errors: EINVAL (bad request, or
+ * larger than the whole budget), EBUSY (queue full and over budget). */
+int mpdata_submit(mpdata_server_t *server, const mpdata_request *req, uint64_t *ticket);
+/* Non-blocking state (MPDATA_REQ_*).  ENOENT for an unknown ticket. */
+int mpdata_poll(mpdata_server_t *server, uint64_t ticket, int *state);
+/* Block until the request finishes or timeout_ms passes (< 0: no limit).
+ * Returns OK (done), ETIMEDOUT, ECANCELED, ENOENT, or the failure code
+ * (ENOMEM when admission could not allocate, ECUDA). */
+int mpdata_wait(mpdata_server_t *server, uint64_t ticket, int timeout_ms);
+/* Cancel a queued or running request (takes effect at the next tick). */
+int mpdata_cancel(mpdata_server_t *server, uint64_t ticket);
+/* Submit, admit and finish times of a request, seconds since server start. */
+int mpdata_request_times(mpdata_server_t *server, uint64_t ticket, double *t3);
+/* stats[0..5]: completed, cell-steps done, admitted bytes, queued, resident,
+ * seconds since start. */
+int mpdata_server_stats(mpdata_server_t *server, double *stats);
+/* Cancel queued work, stop the scheduler, free everything. */
+int mpdata_server_destroy(mpdata_server_t *server);
+
+/* ---- functional-performance-model partitioning (§2-§4) ----
+ * A speed function is a table of npts measured points (xs[i], ss[i]), sizes
+ * increasing, speeds > 0 (work units per second of one processor running a
+ * workload of size xs[i] while all processors run); it is linearly
+ * interpolated and never extrapolated.  Execution time of x is x / s(x). */
+
+/* Algorithm 1 (§4) as printed: n units over an even number p of identical
+ * processors, each a multiple of dx (n/p must be one); p/2 processors take
+ * *x_left and p/2 take *x_right, minimising the larger execution time
+ * *t_min.  The loop bound is read as "while x_left - dx > 0".
+ * Errors: EINVAL. */
+int mpdata_fpm_algorithm1(double n, int p, double dx, const double *xs, const double *ss, int npts,
+                          double *x_left, double *x_right, double *t_min);
+/* Generalisation to any p: *k_right processors take *x_right >= n/p and the
+ * other p - k_right take *x_left = (n - k x_right)/(p - k), both multiples of
+ * dx; k_right = 0 means the balanced split n/p.  Errors: EINVAL (including
+ * "no split fits the table"). */
+int mpdata_fpm_partition(double n, int p, double dx, const double *xs, const double *ss, int npts,
+                         int *k_right, double *x_left, double *x_right, double *t_min);
+/* Condition (2) of §3 on a table: returns 1 (and the two sizes) if some
+ * larger workload has a higher speed-to-size ratio -- load balancing is then
+ * not guaranteed optimal -- 0 if condition (1) holds on the table, < 0 on
+ * error. */
+int mpdata_fpm_condition2(const double *xs, const double *ss, int npts, double *x_at, double *x_more);
+
 /* Name of an error code. */
 const char *mpdata_strerror(int code);
 

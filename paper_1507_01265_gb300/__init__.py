@@ -128,3 +128,177 @@ class Solver:
 
     def __exit__(self, *exc):
         self.close()
+
+
+class Batch:
+    """Many independent FP32 grids advanced together by persistent launches
+    (mpdata_batch_*).  `grids` is a list of (nx, ny, nz) or (nx, ny, nz,
+    (px, py, pz)); fields are attached per grid with set_fields."""
+
+    VARIANTS = 3  # 0: two-column periodic x/y, 1: two-column with a lid, 2: one-column
+
+    def __init__(self, grids, *, nonoscillatory: bool = True, tile=(32, 24), eps: float = 1e-15,
+                 periodic=(1, 1, 1)):
+        o = _lib.default_opts()
+        o.nonoscillatory = int(bool(nonoscillatory))
+        o.tile_x, o.tile_y = int(tile[0]), int(tile[1])
+        o.eps = float(eps)
+        for d in range(3):
+            o.periodic[d] = int(periodic[d])
+        n = len(grids)
+        dims = (ctypes.c_int * (3 * n))()
+        per = (ctypes.c_int * (3 * n))()
+        self.shapes = []
+        for i, gdef in enumerate(grids):
+            nx, ny, nz = (int(v) for v in gdef[:3])
+            p = gdef[3] if len(gdef) > 3 else periodic
+            dims[3 * i:3 * i + 3] = [nx, ny, nz]
+            per[3 * i:3 * i + 3] = [int(v) for v in p]
+            self.shapes.append((nz, ny, nx))
+        self._h = ctypes.c_void_p()
+        check(_lib.lib.mpdata_batch_create(n, dims, per, ctypes.byref(o), ctypes.byref(self._h)),
+              "mpdata_batch_create")
+        self._keep = {}
+
+    def set_fields(self, i, h, psi, u1, u2, u3) -> None:
+        torch = _torch()
+        ptrs = []
+        for t, name in ((h, "h"), (psi, "psi"), (u1, "u1"), (u2, "u2"), (u3, "u3")):
+            if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float32 \
+                    or not t.is_contiguous():
+                raise ValueError("%s of grid %d must be a contiguous float32 CUDA tensor" % (name, i))
+            if t.numel() != self.shapes[i][0] * self.shapes[i][1] * self.shapes[i][2]:
+                raise ValueError("%s of grid %d has the wrong size" % (name, i))
+            ptrs.append(ctypes.c_void_p(t.data_ptr()))
+        self._keep[i] = (h, psi, u1, u2, u3)
+        check(_lib.lib.mpdata_batch_set_fields(self._h, int(i), *ptrs), "mpdata_batch_set_fields")
+
+    def work(self, variant):
+        n, c = ctypes.c_int(), ctypes.c_int()
+        check(_lib.lib.mpdata_batch_work(self._h, int(variant), ctypes.byref(n), ctypes.byref(c)),
+              "mpdata_batch_work")
+        return n.value, c.value
+
+    def get_split(self, variant):
+        _, ncta = self.work(variant)
+        buf = (ctypes.c_int * (ncta + 1))()
+        check(_lib.lib.mpdata_batch_get_split(self._h, int(variant), buf), "mpdata_batch_get_split")
+        return list(buf)
+
+    def set_split(self, variant, begin) -> None:
+        begin = [int(v) for v in begin]
+        buf = (ctypes.c_int * len(begin))(*begin)
+        check(_lib.lib.mpdata_batch_set_split(self._h, int(variant), len(begin) - 1, buf),
+              "mpdata_batch_set_split")
+
+    def step(self, nsteps: int, graph: bool = False, stream=None) -> None:
+        check(_lib.lib.mpdata_batch_step(self._h, int(nsteps), int(bool(graph)),
+                                         _stream_handle(stream)), "mpdata_batch_step")
+
+    def close(self) -> None:
+        if getattr(self, "_h", None) is not None and self._h.value:
+            _lib.lib.mpdata_batch_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+class Server:
+    """Continuous-batching server (mpdata_server_*): submit FP32 host fields,
+    get a ticket, wait for psi to be written back in place."""
+
+    def __init__(self, hbm_budget_bytes: int = 8 << 30, *, max_active: int = 256,
+                 max_queued: int = 1 << 20, chunk_steps: int = 8, tile_y: int = 24,
+                 nonoscillatory: bool = True, inject_alloc_failure: int = 0, eps: float = 1e-15):
+        o = _lib.ServerOpts()
+        _lib.lib.mpdata_server_opts_default(ctypes.byref(o))
+        o.hbm_budget_bytes = int(hbm_budget_bytes)
+        o.max_active, o.max_queued, o.chunk_steps = int(max_active), int(max_queued), int(chunk_steps)
+        o.tile_y, o.nonoscillatory = int(tile_y), int(bool(nonoscillatory))
+        o.inject_alloc_failure, o.eps = int(inject_alloc_failure), float(eps)
+        self._h = ctypes.c_void_p()
+        check(_lib.lib.mpdata_server_create(ctypes.byref(o), ctypes.byref(self._h)),
+              "mpdata_server_create")
+        self._keep = {}
+
+    @staticmethod
+    def _ptr(a, n, name):
+        import numpy as np
+        torch = _torch()
+        if isinstance(a, torch.Tensor):
+            if a.is_cuda or a.dtype != torch.float32 or not a.is_contiguous() or a.numel() != n:
+                raise ValueError("%s must be a contiguous float32 CPU tensor of %d elements" % (name, n))
+            return a.data_ptr()
+        if a.dtype != np.float32 or not a.flags.c_contiguous or a.size != n:
+            raise ValueError("%s must be a contiguous float32 array of %d elements" % (name, n))
+        return a.ctypes.data
+
+    def submit(self, h, psi, u1, u2, u3, nsteps: int, periodic=(1, 1, 1), shape=None) -> int:
+        """Queue a solve; psi (host) receives the result.  shape = (nz, ny, nx)
+        defaults to psi.shape."""
+        nz, ny, nx = shape if shape is not None else tuple(psi.shape)
+        n = nx * ny * nz
+        r = _lib.Request()
+        r.size = ctypes.sizeof(_lib.Request)
+        r.nx, r.ny, r.nz, r.nsteps = int(nx), int(ny), int(nz), int(nsteps)
+        for d in range(3):
+            r.periodic[d] = int(periodic[d])
+        r.h, r.u1, r.u2, r.u3 = (self._ptr(a, n, nm) for a, nm in ((h, "h"), (u1, "u1"), (u2, "u2"), (u3, "u3")))
+        r.psi = self._ptr(psi, n, "psi")
+        t = ctypes.c_uint64()
+        check(_lib.lib.mpdata_submit(self._h, ctypes.byref(r), ctypes.byref(t)), "mpdata_submit")
+        self._keep[t.value] = (h, psi, u1, u2, u3)
+        return t.value
+
+    def poll(self, ticket: int) -> int:
+        st = ctypes.c_int()
+        check(_lib.lib.mpdata_poll(self._h, ctypes.c_uint64(ticket), ctypes.byref(st)), "mpdata_poll")
+        return st.value
+
+    def wait(self, ticket: int, timeout_ms: int = -1) -> None:
+        rc = _lib.lib.mpdata_wait(self._h, ctypes.c_uint64(ticket), int(timeout_ms))
+        if rc == _lib.MPDATA_OK:
+            self._keep.pop(ticket, None)
+        check(rc, "mpdata_wait")
+
+    def cancel(self, ticket: int) -> None:
+        check(_lib.lib.mpdata_cancel(self._h, ctypes.c_uint64(ticket)), "mpdata_cancel")
+
+    def times(self, ticket: int):
+        """(submit, admit, done) in seconds since the server started."""
+        t = (ctypes.c_double * 3)()
+        check(_lib.lib.mpdata_request_times(self._h, ctypes.c_uint64(ticket), t), "mpdata_request_times")
+        return tuple(t)
+
+    def stats(self) -> dict:
+        v = (ctypes.c_double * 6)()
+        check(_lib.lib.mpdata_server_stats(self._h, v), "mpdata_server_stats")
+        return {"completed": int(v[0]), "cell_steps": v[1], "admitted_bytes": int(v[2]),
+                "queued": int(v[3]), "resident": int(v[4]), "uptime_s": v[5]}
+
+    def close(self) -> None:
+        if getattr(self, "_h", None) is not None and self._h.value:
+            _lib.lib.mpdata_server_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -35,6 +35,24 @@ class Opts(ctypes.Structure):
                 ("tile_x", ctypes.c_int32), ("tile_y", ctypes.c_int32), ("eps", ctypes.c_double)]
 
 
+class ServerOpts(ctypes.Structure):
+    _fields_ = [("size", ctypes.c_uint32), ("hbm_budget_bytes", ctypes.c_size_t),
+                ("max_active", ctypes.c_int32), ("max_queued", ctypes.c_int32),
+                ("chunk_steps", ctypes.c_int32), ("tile_y", ctypes.c_int32),
+                ("nonoscillatory", ctypes.c_int32), ("inject_alloc_failure", ctypes.c_int32),
+                ("eps", ctypes.c_double)]
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("size", ctypes.c_uint32), ("nx", ctypes.c_int32), ("ny", ctypes.c_int32),
+                ("nz", ctypes.c_int32), ("periodic", ctypes.c_int32 * 3), ("nsteps", ctypes.c_int32),
+                ("h", ctypes.c_void_p), ("u1", ctypes.c_void_p), ("u2", ctypes.c_void_p),
+                ("u3", ctypes.c_void_p), ("psi", ctypes.c_void_p)]
+
+
+REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_FAILED, REQ_CANCELLED = range(5)
+
+
 class MpdataError(RuntimeError):
     def __init__(self, code: int, what: str):
         self.code = code
@@ -46,7 +64,8 @@ def _load():
         raise ImportError("libmpdata.so is not built (%s); run "
                           "`python -c 'import __graft_entry__ as g; g.build()'`" % LIB_PATH)
     lib = ctypes.CDLL(LIB_PATH)
-    P, I, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    P, I = ctypes.c_void_p, ctypes.c_int
+    D = ctypes.c_double
     H = ctypes.c_void_p  # mpdata_t*
     sig = {
         "mpdata_opts_default": (None, [ctypes.POINTER(Opts)]),
@@ -56,6 +75,25 @@ def _load():
         "mpdata_solve_host": (I, [H, P, P, P, P, P, I, P]),
         "mpdata_mass": (I, [H, P, P, P, P]),
         "mpdata_mass_noalloc": (I, [P, P, ctypes.c_longlong, I, P, P]),
+        "mpdata_batch_create": (I, [I, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(Opts), ctypes.POINTER(H)]),
+        "mpdata_batch_set_fields": (I, [H, I, P, P, P, P, P]),
+        "mpdata_batch_work": (I, [H, I, ctypes.POINTER(I), ctypes.POINTER(I)]),
+        "mpdata_batch_get_split": (I, [H, I, ctypes.POINTER(I)]),
+        "mpdata_batch_set_split": (I, [H, I, I, ctypes.POINTER(I)]),
+        "mpdata_batch_step": (I, [H, I, I, P]),
+        "mpdata_batch_destroy": (I, [H]),
+        "mpdata_server_opts_default": (None, [ctypes.POINTER(ServerOpts)]),
+        "mpdata_server_create": (I, [ctypes.POINTER(ServerOpts), ctypes.POINTER(H)]),
+        "mpdata_submit": (I, [H, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_uint64)]),
+        "mpdata_poll": (I, [H, ctypes.c_uint64, ctypes.POINTER(I)]),
+        "mpdata_wait": (I, [H, ctypes.c_uint64, I]),
+        "mpdata_cancel": (I, [H, ctypes.c_uint64]),
+        "mpdata_request_times": (I, [H, ctypes.c_uint64, ctypes.POINTER(ctypes.c_double)]),
+        "mpdata_server_stats": (I, [H, ctypes.POINTER(ctypes.c_double)]),
+        "mpdata_server_destroy": (I, [H]),
+        "mpdata_fpm_algorithm1": (I, [D, I, D, P, P, I, ctypes.POINTER(D), ctypes.POINTER(D), ctypes.POINTER(D)]),
+        "mpdata_fpm_partition": (I, [D, I, D, P, P, I, ctypes.POINTER(I), ctypes.POINTER(D), ctypes.POINTER(D), ctypes.POINTER(D)]),
+        "mpdata_fpm_condition2": (I, [P, P, I, ctypes.POINTER(D), ctypes.POINTER(D)]),
         "mpdata_strerror": (ctypes.c_char_p, [I]),
         "mpdata_last_error_message": (ctypes.c_char_p, []),
         "mpdata_version": (ctypes.c_char_p, []),
@@ -64,7 +102,6 @@ def _load():
         f = getattr(lib, name)
         f.restype = res
         f.argtypes = args
-    _ = D
     return lib
 
 

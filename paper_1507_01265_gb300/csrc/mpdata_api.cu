@@ -41,6 +41,15 @@ int fail(int code, const char *fmt, ...) {
     return code;
 }
 
+}  // namespace
+
+int mpdata::set_error(int code, const char *message) {
+    g_last_error = message;
+    return code;
+}
+
+namespace {
+
 int cuda_fail(cudaError_t e, const char *what) {
     return fail(MPDATA_ECUDA, "%s: %s (%s)", what, cudaGetErrorName(e), cudaGetErrorString(e));
 }

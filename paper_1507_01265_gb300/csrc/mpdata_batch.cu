@@ -1,0 +1,317 @@
+// Batched persistent launch of many independent grids (C ABI in
+// include/mpdata.h: mpdata_batch_*).
+//
+// Every grid is cut into the same tiles as a single-grid launch.  Tiles of
+// all grids that use the same kernel variant form one work-item list
+// (grid, tile); a persistent launch of one CTA per SM runs the list, CTA c
+// taking the contiguous items [begin[c], begin[c+1]).  The default split
+// balances the estimated cost (tile area x (nz + 3) planes); callers (the
+// speed-function autotuner) may install any other split, including uneven
+// ones.  A step of the batch is one launch per variant; nsteps steps can be
+// captured once into a CUDA graph and replayed.  Each tile is computed by the
+// same code whichever CTA runs it, so every grid's result is bit-identical to
+// the single-grid launch.
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <map>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "mpdata_internal.cuh"
+
+using mpdata::BatchGrid;
+using mpdata::Grid;
+
+namespace {
+
+enum Variant { kPairsPeriodic = 0, kPairsLid = 1, kSingle = 2, kNumVariants = 3 };
+
+struct Group {
+    std::vector<int2> items;  // (grid, tile)
+    std::vector<int> begin;   // ncta + 1
+    int2 *d_items = nullptr;
+    int *d_begin = nullptr;
+    int ncta = 0;
+    bool dirty = true;
+};
+
+}  // namespace
+
+struct mpdata_batch {
+    int ngrids = 0;
+    mpdata_opts opts;
+    int tile_x = 32, tile_y = 24;
+    int nsm = 0;
+    std::vector<BatchGrid> grids;    // host copy of the descriptors
+    std::vector<int> variant;        // per grid
+    std::vector<size_t> bytes;       // per grid psi size
+    std::vector<bool> has_fields;
+    BatchGrid *d_grids = nullptr;
+    bool grids_dirty = true;
+    Group group[kNumVariants];
+    cudaStream_t capture_stream = nullptr;
+    std::map<int, cudaGraphExec_t> graphs;  // by nsteps
+    std::map<int, cudaGraph_t> graph_defs;
+};
+
+namespace {
+
+int bfail(int code, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    return mpdata::set_error(code, buf);
+}
+
+int bcuda(cudaError_t e, const char *what) {
+    return bfail(MPDATA_ECUDA, "%s: %s (%s)", what, cudaGetErrorName(e), cudaGetErrorString(e));
+}
+
+void drop_graphs(mpdata_batch *b) {
+    for (auto &kv : b->graphs) cudaGraphExecDestroy(kv.second);
+    for (auto &kv : b->graph_defs) cudaGraphDestroy(kv.second);
+    b->graphs.clear();
+    b->graph_defs.clear();
+}
+
+// Split items into ncta contiguous ranges of (nearly) equal total cost: the
+// boundary of CTA c sits at the item boundary closest to c/ncta of the total.
+void balanced_split(const std::vector<double> &cost, int ncta, std::vector<int> &begin) {
+    const int n = (int)cost.size();
+    std::vector<double> prefix(n + 1, 0.0);
+    for (int i = 0; i < n; ++i) prefix[i + 1] = prefix[i] + cost[i];
+    begin.assign(ncta + 1, 0);
+    for (int c = 1; c < ncta; ++c) {
+        const double target = prefix[n] * c / ncta;
+        int i = (int)(std::lower_bound(prefix.begin(), prefix.end(), target) - prefix.begin());
+        if (i > 0 && target - prefix[i - 1] < prefix[i] - target) --i;
+        begin[c] = std::max(begin[c - 1], std::min(i, n));
+    }
+    begin[ncta] = n;
+}
+
+double item_cost(const BatchGrid &g, int tx, int ty) { return (double)tx * ty * (g.g.nz + 3); }
+
+int upload_group(mpdata_batch *b, int v) {
+    Group &G = b->group[v];
+    if (!G.dirty) return MPDATA_OK;
+    cudaFree(G.d_items);
+    cudaFree(G.d_begin);
+    G.d_items = nullptr;
+    G.d_begin = nullptr;
+    if (G.items.empty()) { G.dirty = false; return MPDATA_OK; }
+    cudaError_t e = cudaMalloc((void **)&G.d_items, sizeof(int2) * G.items.size());
+    if (e == cudaSuccess) e = cudaMalloc((void **)&G.d_begin, sizeof(int) * G.begin.size());
+    if (e == cudaSuccess) e = cudaMemcpy(G.d_items, G.items.data(), sizeof(int2) * G.items.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(G.d_begin, G.begin.data(), sizeof(int) * G.begin.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return bcuda(e, "batch work-list upload");
+    G.dirty = false;
+    return MPDATA_OK;
+}
+
+int enqueue_steps(mpdata_batch *b, int nsteps, cudaStream_t s) {
+    if (nsteps & 1) {
+        for (int i = 0; i < b->ngrids; ++i) {
+            cudaError_t e = cudaMemcpyAsync(b->grids[i].buf[1], b->grids[i].buf[0], b->bytes[i],
+                                            cudaMemcpyDeviceToDevice, s);
+            if (e != cudaSuccess) return bcuda(e, "cudaMemcpyAsync");
+        }
+    }
+    for (int st = 0; st < nsteps; ++st) {
+        const int parity = (nsteps & 1) ? ((st + 1) & 1) : (st & 1);
+        for (int v = 0; v < kNumVariants; ++v) {
+            Group &G = b->group[v];
+            if (G.items.empty()) continue;
+            cudaError_t e;
+            if (v == kSingle)
+                e = mpdata::launch_fused_single_batch(b->opts.nonoscillatory, b->d_grids, G.d_items,
+                                                      G.d_begin, G.ncta, parity, s);
+            else
+                e = mpdata::launch_fused_pairs_batch(b->tile_x, b->tile_y, b->opts.nonoscillatory,
+                                                     v == kPairsLid, b->d_grids, G.d_items, G.d_begin,
+                                                     G.ncta, parity, s);
+            if (e != cudaSuccess) return bcuda(e, "batched kernel launch");
+        }
+    }
+    return MPDATA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int mpdata_batch_create(int ngrids, const int *dims, const int *periodic, const mpdata_opts *opts,
+                        mpdata_batch_t **out) {
+    if (!out) return bfail(MPDATA_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (ngrids < 1 || !dims) return bfail(MPDATA_EINVAL, "need ngrids >= 1 and dims");
+    mpdata_opts o;
+    if (opts) o = *opts; else mpdata_opts_default(&o);
+    if (o.size < sizeof(mpdata_opts)) return bfail(MPDATA_EINVAL, "opts.size too small");
+    if (o.dtype != MPDATA_F32 || o.iterations != 2 || o.path != MPDATA_PATH_FUSED)
+        return bfail(MPDATA_EINVAL, "batches run the FP32 fused step with 2 iterations");
+    if (!(o.eps > 0.0)) return bfail(MPDATA_EINVAL, "eps must be > 0");
+    int tx = o.tile_x ? o.tile_x : 32, ty = o.tile_y ? o.tile_y : 24;
+    if (!(tx == 32 && (ty == 16 || ty == 24))) return bfail(MPDATA_EINVAL, "batch tile must be 32x16 or 32x24");
+
+    mpdata_batch *b = new (std::nothrow) mpdata_batch();
+    if (!b) return bfail(MPDATA_ENOMEM, "host allocation failed");
+    b->ngrids = ngrids;
+    b->opts = o;
+    b->tile_x = tx;
+    b->tile_y = ty;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaError_t e = cudaDeviceGetAttribute(&b->nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) { delete b; return bcuda(e, "cudaDeviceGetAttribute"); }
+    b->grids.resize(ngrids);
+    b->variant.resize(ngrids);
+    b->bytes.resize(ngrids);
+    b->has_fields.assign(ngrids, false);
+    std::vector<std::vector<double>> costs(kNumVariants);
+    for (int i = 0; i < ngrids; ++i) {
+        const int nx = dims[3 * i], ny = dims[3 * i + 1], nz = dims[3 * i + 2];
+        if (nx < 1 || ny < 1 || nz < 1 || ny > 65535 || nz > 65535 || (long long)nx * ny * nz >= (1LL << 31)) {
+            mpdata_batch_destroy(b);
+            return bfail(MPDATA_EINVAL, "grid %d has bad dims %d x %d x %d", i, nx, ny, nz);
+        }
+        BatchGrid &g = b->grids[i];
+        memset(&g, 0, sizeof g);
+        g.g.nx = nx; g.g.ny = ny; g.g.nz = nz;
+        for (int d = 0; d < 3; ++d) {
+            int p = periodic ? periodic[3 * i + d] : o.periodic[d];
+            if (p != 0 && p != 1) { mpdata_batch_destroy(b); return bfail(MPDATA_EINVAL, "periodic flags must be 0 or 1"); }
+            g.g.per[d] = p;
+        }
+        g.eps = (float)o.eps;
+        int v = mpdata::fused_pairs_supported(g.g, tx, ty) ? ((!g.g.per[0] || !g.g.per[1]) ? kPairsLid : kPairsPeriodic) : kSingle;
+        const int gtx = v == kSingle ? 32 : tx, gty = v == kSingle ? 16 : ty;
+        g.ntx = (nx + gtx - 1) / gtx;
+        const int ntiles = g.ntx * ((ny + gty - 1) / gty);
+        b->variant[i] = v;
+        b->bytes[i] = (size_t)nx * ny * nz * sizeof(float);
+        for (int tl = 0; tl < ntiles; ++tl) {
+            b->group[v].items.push_back(make_int2(i, tl));
+            costs[v].push_back(item_cost(g, gtx, gty));
+        }
+        e = cudaMalloc((void **)&g.buf[1], b->bytes[i]);  // scratch partner of psi
+        if (e != cudaSuccess) { cudaGetLastError(); mpdata_batch_destroy(b); return bfail(MPDATA_ENOMEM, "scratch allocation for grid %d failed", i); }
+    }
+    for (int v = 0; v < kNumVariants; ++v) {
+        Group &G = b->group[v];
+        G.ncta = G.items.empty() ? 0 : (int)std::min<size_t>(G.items.size(), (size_t)b->nsm);
+        if (G.ncta) balanced_split(costs[v], G.ncta, G.begin);
+    }
+    e = cudaMalloc((void **)&b->d_grids, sizeof(BatchGrid) * ngrids);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->capture_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) { mpdata_batch_destroy(b); return bcuda(e, "batch allocation"); }
+    *out = b;
+    return MPDATA_OK;
+}
+
+int mpdata_batch_set_fields(mpdata_batch_t *b, int grid, const void *h, void *psi, const void *u1,
+                            const void *u2, const void *u3) {
+    if (!b) return bfail(MPDATA_EINVAL, "batch is NULL");
+    if (grid < 0 || grid >= b->ngrids) return bfail(MPDATA_EINVAL, "grid index %d out of range", grid);
+    const void *p[5] = {h, psi, u1, u2, u3};
+    for (int f = 0; f < 5; ++f)
+        if (!p[f] || ((uintptr_t)p[f] & 15u)) return bfail(MPDATA_EINVAL, "field pointers must be non-NULL and 16-byte aligned");
+    BatchGrid &g = b->grids[grid];
+    g.h = (const float *)h;
+    g.u1 = (const float *)u1;
+    g.u2 = (const float *)u2;
+    g.u3 = (const float *)u3;
+    g.buf[0] = (float *)psi;
+    b->has_fields[grid] = true;
+    b->grids_dirty = true;
+    drop_graphs(b);
+    return MPDATA_OK;
+}
+
+int mpdata_batch_work(mpdata_batch_t *b, int variant, int *nitems, int *ncta) {
+    if (!b || variant < 0 || variant >= kNumVariants) return bfail(MPDATA_EINVAL, "bad batch or variant");
+    if (nitems) *nitems = (int)b->group[variant].items.size();
+    if (ncta) *ncta = b->group[variant].ncta;
+    return MPDATA_OK;
+}
+
+int mpdata_batch_get_split(mpdata_batch_t *b, int variant, int *begin) {
+    if (!b || variant < 0 || variant >= kNumVariants || !begin) return bfail(MPDATA_EINVAL, "bad arguments");
+    const Group &G = b->group[variant];
+    for (size_t i = 0; i < G.begin.size(); ++i) begin[i] = G.begin[i];
+    return MPDATA_OK;
+}
+
+int mpdata_batch_set_split(mpdata_batch_t *b, int variant, int ncta, const int *begin) {
+    if (!b || variant < 0 || variant >= kNumVariants || !begin) return bfail(MPDATA_EINVAL, "bad arguments");
+    Group &G = b->group[variant];
+    const int n = (int)G.items.size();
+    if (ncta < 1 || begin[0] != 0 || begin[ncta] != n)
+        return bfail(MPDATA_EINVAL, "split must have ncta >= 1, begin[0] = 0, begin[ncta] = %d", n);
+    for (int c = 0; c < ncta; ++c)
+        if (begin[c + 1] < begin[c]) return bfail(MPDATA_EINVAL, "split offsets must be nondecreasing");
+    G.begin.assign(begin, begin + ncta + 1);
+    G.ncta = ncta;
+    G.dirty = true;
+    drop_graphs(b);
+    return MPDATA_OK;
+}
+
+int mpdata_batch_step(mpdata_batch_t *b, int nsteps, int use_graph, void *stream) {
+    if (!b) return bfail(MPDATA_EINVAL, "batch is NULL");
+    if (nsteps < 0) return bfail(MPDATA_EINVAL, "nsteps must be >= 0");
+    for (int i = 0; i < b->ngrids; ++i)
+        if (!b->has_fields[i]) return bfail(MPDATA_EINVAL, "grid %d has no fields (mpdata_batch_set_fields)", i);
+    if (nsteps == 0) return MPDATA_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (b->grids_dirty) {
+        cudaError_t e = cudaMemcpyAsync(b->d_grids, b->grids.data(), sizeof(BatchGrid) * b->ngrids,
+                                        cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) return bcuda(e, "descriptor upload");
+        e = cudaStreamSynchronize(s);  // the host copy may change after return
+        if (e != cudaSuccess) return bcuda(e, "descriptor upload");
+        b->grids_dirty = false;
+    }
+    for (int v = 0; v < kNumVariants; ++v) {
+        int rc = upload_group(b, v);
+        if (rc) return rc;
+    }
+    if (!use_graph) return enqueue_steps(b, nsteps, s);
+    auto it = b->graphs.find(nsteps);
+    if (it == b->graphs.end()) {
+        cudaStream_t cs = b->capture_stream;
+        cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return bcuda(e, "cudaStreamBeginCapture");
+        int rc = enqueue_steps(b, nsteps, cs);
+        cudaGraph_t graph = nullptr;
+        e = cudaStreamEndCapture(cs, &graph);
+        if (rc) { if (graph) cudaGraphDestroy(graph); return rc; }
+        if (e != cudaSuccess) return bcuda(e, "cudaStreamEndCapture");
+        cudaGraphExec_t exec = nullptr;
+        e = cudaGraphInstantiate(&exec, graph, 0);
+        if (e != cudaSuccess) { cudaGraphDestroy(graph); return bcuda(e, "cudaGraphInstantiate"); }
+        b->graph_defs[nsteps] = graph;
+        it = b->graphs.emplace(nsteps, exec).first;
+    }
+    cudaError_t e = cudaGraphLaunch(it->second, s);
+    return e == cudaSuccess ? MPDATA_OK : bcuda(e, "cudaGraphLaunch");
+}
+
+int mpdata_batch_destroy(mpdata_batch_t *b) {
+    if (!b) return MPDATA_OK;
+    drop_graphs(b);
+    for (auto &g : b->grids) cudaFree(g.buf[1]);
+    for (auto &G : b->group) { cudaFree(G.d_items); cudaFree(G.d_begin); }
+    cudaFree(b->d_grids);
+    if (b->capture_stream) cudaStreamDestroy(b->capture_stream);
+    delete b;
+    return MPDATA_OK;
+}
+
+}  // extern "C"

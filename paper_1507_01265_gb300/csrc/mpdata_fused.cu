@@ -134,15 +134,15 @@ __device__ __forceinline__ T pseudo_velocity(T U, T pR, T pL, T spa, T sma, T ua
     return (fabs(U) - U * U * r) * A - U * cross * r;
 }
 
+// One tile (index `tile`, row-major with ntx tiles per row) marched through
+// all z planes by the whole CTA.
 template <typename T, int TX, int TY, bool NONOSC>
-__global__ void __launch_bounds__(Layout<TX, TY>::NT, 1)
-    k_fused(Grid g, T eps, int ntx, const T *__restrict__ h, const T *__restrict__ psi,
-            const T *__restrict__ u1, const T *__restrict__ u2, const T *__restrict__ u3,
-            T *__restrict__ out) {
+__device__ __forceinline__ void single_tile(const Grid &g, T eps, int ntx, const T *__restrict__ h,
+                                            const T *__restrict__ psi, const T *__restrict__ u1,
+                                            const T *__restrict__ u2, const T *__restrict__ u3,
+                                            T *__restrict__ out, int tile, T *const sm) {
     using L = Layout<TX, TY>;
     constexpr int EX = L::EX, PL = L::PL, NT = L::NT;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    T *const sm = reinterpret_cast<T *>(smem_raw);
     const unsigned sm_base = (unsigned)__cvta_generic_to_shared(sm);
 #define PLANE(k) (sm + (k) * PL)
 #define RING(f, q) PLANE(L::RING + (f) * 4 + ((q) & 3))
@@ -151,7 +151,7 @@ __global__ void __launch_bounds__(Layout<TX, TY>::NT, 1)
     const int nx = g.nx, ny = g.ny, nz = g.nz;
     const int perx = g.per[0], pery = g.per[1], perz = g.per[2];
     const long long nxy = (long long)nx * ny;
-    const int x0 = (blockIdx.x % ntx) * TX, y0 = (blockIdx.x / ntx) * TY;
+    const int x0 = (tile % ntx) * TX, y0 = (tile / ntx) * TY;
 
     // ---- this thread's column and its neighbour indices in the plane ----
     int rx, ry;
@@ -383,8 +383,36 @@ __global__ void __launch_bounds__(Layout<TX, TY>::NT, 1)
         bd_prev = bd_c;
     }
     asm volatile("cp.async.wait_all;\n" ::: "memory");
+    __syncthreads();  // shared memory is reused by the next tile of a persistent CTA
 #undef RING
 #undef PLANE
+}
+
+template <typename T, int TX, int TY, bool NONOSC>
+__global__ void __launch_bounds__(Layout<TX, TY>::NT, 1)
+    k_fused(Grid g, T eps, int ntx, const T *__restrict__ h, const T *__restrict__ psi,
+            const T *__restrict__ u1, const T *__restrict__ u2, const T *__restrict__ u3,
+            T *__restrict__ out) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    single_tile<T, TX, TY, NONOSC>(g, eps, ntx, h, psi, u1, u2, u3, out, blockIdx.x,
+                                   reinterpret_cast<T *>(smem_raw));
+}
+
+// Persistent batched launch (FP32, 32x16 tiles): CTA c runs work items
+// [begin[c], begin[c+1]) of the (grid, tile) list.
+template <bool NONOSC>
+__global__ void __launch_bounds__(Layout<32, 16>::NT, 1)
+    k_fused_single_batch(const BatchGrid *__restrict__ grids, const int2 *__restrict__ items,
+                         const int *__restrict__ begin, int parity) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float *const sm = reinterpret_cast<float *>(smem_raw);
+    const int lo = begin[blockIdx.x], hi = begin[blockIdx.x + 1];
+    for (int it = lo; it < hi; ++it) {
+        const int2 w = items[it];
+        const TileArgs a = batch_args(grids[w.x], parity);
+        single_tile<float, 32, 16, NONOSC>(a.g, a.eps, a.ntx, a.h, a.psi, a.u1, a.u2, a.u3, a.out,
+                                           w.y, sm);
+    }
 }
 
 template <typename T, int TX, int TY>
@@ -403,6 +431,17 @@ cudaError_t launch_tile(const Grid &g, int nonosc, double eps, const void *h, co
 }
 
 }  // namespace
+
+cudaError_t launch_fused_single_batch(int nonosc, const BatchGrid *grids, const int2 *items,
+                                      const int *begin, int ncta, int parity, cudaStream_t s) {
+    using L = Layout<32, 16>;
+    const size_t smem = (size_t)L::NPLANES * L::PL * sizeof(float);
+    auto kern = nonosc ? k_fused_single_batch<true> : k_fused_single_batch<false>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<ncta, L::NT, smem, s>>>(grids, items, begin, parity);
+    return cudaGetLastError();
+}
 
 static bool single_tile_supported(int dtype, int tx, int ty) {
     if (dtype == MPDATA_F64) return (tx == 16 && ty == 16);

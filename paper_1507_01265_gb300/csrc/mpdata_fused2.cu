@@ -156,13 +156,20 @@ __device__ __forceinline__ void stp(unsigned b, F2 v) {
     asm volatile("st.shared.v2.f32 [%0+%1], {%2,%3};" ::"r"(b), "n"(OFF), "f"(v.x), "f"(v.y) : "memory");
 }
 
+// One tile (tile index `tile` of grid a.g, tiles numbered row-major with
+// a.ntx tiles per row) marched through all z planes by the whole CTA.
 template <int TX, int TY, bool NONOSC, bool LID>
-__global__ void __launch_bounds__(Lay2<TX, TY>::NT, 1)
-    k_fused_pairs(Grid g, float eps1, int ntx, const float *__restrict__ h,
-                  const float *__restrict__ psi, const float *__restrict__ u1,
-                  const float *__restrict__ u2, const float *__restrict__ u3,
-                  float *__restrict__ out) {
+__device__ __forceinline__ void pairs_tile(const TileArgs &a, int tile, float *sm) {
     using L = Lay2<TX, TY>;
+    const Grid &g = a.g;
+    const float eps1 = a.eps;
+    const float *__restrict__ h = a.h;
+    const float *__restrict__ psi = a.psi;
+    const float *__restrict__ u1 = a.u1;
+    const float *__restrict__ u2 = a.u2;
+    const float *__restrict__ u3 = a.u3;
+    float *__restrict__ out = a.out;
+    const int ntx = a.ntx;
     constexpr int EX = L::EX, PL = L::PL;
     constexpr int PB = PL * 4;         // bytes per plane
     constexpr int FB = 4 * PB;         // bytes between ring fields
@@ -171,14 +178,13 @@ __global__ void __launch_bounds__(Lay2<TX, TY>::NT, 1)
     constexpr int oP1 = L::P1 * PB, oSX = L::SX * PB, oSY = L::SY * PB, oSZ = L::SZ * PB;
     constexpr int oV1 = L::V1 * PB, oV2 = L::V2 * PB, oBU = L::BU * PB, oBD = L::BD * PB;
     constexpr int oGX = L::GX * PB, oGY = L::GY * PB;
-    extern __shared__ __align__(16) float sm[];
     const unsigned sm_base = (unsigned)__cvta_generic_to_shared(sm);
 
     const int t = threadIdx.x;
     const int nx = g.nx, ny = g.ny, nz = g.nz;
     const int perx = LID ? g.per[0] : 1, pery = LID ? g.per[1] : 1, perz = g.per[2];
     const long long nxy = (long long)nx * ny;
-    const int x0 = (blockIdx.x % ntx) * TX, y0 = (blockIdx.x / ntx) * TY;
+    const int x0 = (tile % ntx) * TX, y0 = (tile / ntx) * TY;
     const F2 eps = bc(eps1);
 
     int px, ry;
@@ -405,6 +411,28 @@ __global__ void __launch_bounds__(Lay2<TX, TY>::NT, 1)
         wlo_v = whi_v; bu_prev = bu_c; bd_prev = bd_c;
     }
     asm volatile("cp.async.wait_all;\n" ::: "memory");
+    __syncthreads();  // shared memory is reused by the next tile of a persistent CTA
+}
+
+template <int TX, int TY, bool NONOSC, bool LID>
+__global__ void __launch_bounds__(Lay2<TX, TY>::NT, 1) k_fused_pairs(TileArgs a) {
+    extern __shared__ __align__(16) float sm[];
+    pairs_tile<TX, TY, NONOSC, LID>(a, blockIdx.x, sm);
+}
+
+// Persistent batched launch: CTA c runs work items [begin[c], begin[c+1]) of
+// the item list, each item a (grid, tile) pair; parity selects which buffer
+// of each grid's (psi, scratch) pair is read.
+template <int TX, int TY, bool NONOSC, bool LID>
+__global__ void __launch_bounds__(Lay2<TX, TY>::NT, 1)
+    k_fused_pairs_batch(const BatchGrid *__restrict__ grids, const int2 *__restrict__ items,
+                        const int *__restrict__ begin, int parity) {
+    extern __shared__ __align__(16) float sm[];
+    const int lo = begin[blockIdx.x], hi = begin[blockIdx.x + 1];
+    for (int it = lo; it < hi; ++it) {
+        const int2 w = items[it];
+        pairs_tile<TX, TY, NONOSC, LID>(batch_args(grids[w.x], parity), w.y, sm);
+    }
 }
 
 template <int TX, int TY>
@@ -418,9 +446,26 @@ cudaError_t launch_pairs(const Grid &g, int nonosc, double eps, const void *h, c
                        : (lid ? k_fused_pairs<TX, TY, false, true> : k_fused_pairs<TX, TY, false, false>);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    kern<<<ntx * nty, L::NT, smem, s>>>(g, (float)eps, ntx, (const float *)h, (const float *)psi,
-                                        (const float *)u1, (const float *)u2, (const float *)u3,
-                                        (float *)out);
+    TileArgs a;
+    a.g = g;
+    a.ntx = ntx;
+    a.eps = (float)eps;
+    a.h = (const float *)h; a.psi = (const float *)psi; a.u1 = (const float *)u1;
+    a.u2 = (const float *)u2; a.u3 = (const float *)u3; a.out = (float *)out;
+    kern<<<ntx * nty, L::NT, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <int TX, int TY>
+cudaError_t launch_pairs_batch(int nonosc, int lid, const BatchGrid *grids, const int2 *items,
+                               const int *begin, int ncta, int parity, cudaStream_t s) {
+    using L = Lay2<TX, TY>;
+    const size_t smem = (size_t)L::NPLANES * L::PL * sizeof(float);
+    auto kern = nonosc ? (lid ? k_fused_pairs_batch<TX, TY, true, true> : k_fused_pairs_batch<TX, TY, true, false>)
+                       : (lid ? k_fused_pairs_batch<TX, TY, false, true> : k_fused_pairs_batch<TX, TY, false, false>);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<ncta, L::NT, smem, s>>>(grids, items, begin, parity);
     return cudaGetLastError();
 }
 
@@ -437,6 +482,14 @@ cudaError_t launch_fused_pairs(const Grid &g, int nonosc, double eps, int tx, in
     if (g.nx % 4 != 0) return cudaErrorInvalidValue;
     if (tx == 32 && ty == 16) return launch_pairs<32, 16>(g, nonosc, eps, h, psi, u1, u2, u3, out, s);
     if (tx == 32 && ty == 24) return launch_pairs<32, 24>(g, nonosc, eps, h, psi, u1, u2, u3, out, s);
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_fused_pairs_batch(int tx, int ty, int nonosc, int lid, const BatchGrid *grids,
+                                     const int2 *items, const int *begin, int ncta, int parity,
+                                     cudaStream_t s) {
+    if (tx == 32 && ty == 16) return launch_pairs_batch<32, 16>(nonosc, lid, grids, items, begin, ncta, parity, s);
+    if (tx == 32 && ty == 24) return launch_pairs_batch<32, 24>(nonosc, lid, grids, items, begin, ncta, parity, s);
     return cudaErrorInvalidValue;
 }
 

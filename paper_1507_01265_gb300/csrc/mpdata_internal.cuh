@@ -31,6 +31,36 @@ __device__ __forceinline__ T upstream_flux(T U, T L, T R) {
     return U > T(0) ? U * L : U * R;
 }
 
+// Arguments of one grid for a fused tile body (FP32).
+struct TileArgs {
+    Grid g;
+    int ntx;  // tiles per row of this grid
+    float eps;
+    const float *h, *psi, *u1, *u2, *u3;
+    float *out;
+};
+
+// One grid of a batched launch: both buffers of its psi ping-pong pair; the
+// launch's parity picks which one is read.
+struct BatchGrid {
+    Grid g;
+    int ntx;
+    float eps;
+    const float *h, *u1, *u2, *u3;
+    float *buf[2];
+};
+
+__host__ __device__ inline TileArgs batch_args(const BatchGrid &b, int parity) {
+    TileArgs a;
+    a.g = b.g;
+    a.ntx = b.ntx;
+    a.eps = b.eps;
+    a.h = b.h; a.u1 = b.u1; a.u2 = b.u2; a.u3 = b.u3;
+    a.psi = b.buf[parity];
+    a.out = b.buf[parity ^ 1];
+    return a;
+}
+
 // Launchers of the stage-per-kernel path (mpdata_stages.cu).
 struct StageBuffers {
     void *psi1, *v1, *v2, *v3, *bup, *bdn;
@@ -51,9 +81,18 @@ cudaError_t launch_fused_step(int dtype, const Grid &g, int nonosc, double eps, 
 bool fused_tile_supported(int dtype, const Grid &g, int tile_x, int tile_y);
 void fused_default_tile(int dtype, const Grid &g, int *tile_x, int *tile_y);
 bool fused_pairs_supported(const Grid &g, int tile_x, int tile_y);
+// Persistent batched launches (ncta CTAs; CTA c runs items [begin[c], begin[c+1])).
+cudaError_t launch_fused_pairs_batch(int tile_x, int tile_y, int nonosc, int lid,
+                                     const BatchGrid *grids, const int2 *items, const int *begin,
+                                     int ncta, int parity, cudaStream_t s);
+cudaError_t launch_fused_single_batch(int nonosc, const BatchGrid *grids, const int2 *items,
+                                      const int *begin, int ncta, int parity, cudaStream_t s);
 cudaError_t launch_fused_pairs(const Grid &g, int nonosc, double eps, int tile_x, int tile_y,
                                const void *h, const void *psi, const void *u1, const void *u2,
                                const void *u3, void *out, cudaStream_t s);
+
+// Record the calling thread's last error message (mpdata_api.cu); returns code.
+int set_error(int code, const char *message);
 
 // Deterministic FP64 diagnostics (mpdata_reduce.cu).
 constexpr int kReduceBlocks = 1024;  // fixed, so the summation tree never changes

@@ -1,0 +1,130 @@
+"""Speed-function autotuner for the persistent batched launch (§5.4, §4).
+
+The paper builds speed functions of its core teams by timing every team at
+once on equal workloads (so contention is included, §5.4), then feeds them
+to Algorithm 1 to pick a possibly uneven partition.  The GPU analogue here:
+
+  * a "processor" is one persistent CTA (one per SM) and its workload x is
+    the number of tiles it marches;
+  * s(x) is measured with all CTAs busy: a synthetic grid of exactly P*x
+    tiles (P = number of SMs), so the balanced split gives every CTA x tiles;
+    s(x) = x * (tile cells) / (time of one step), cells per second per CTA;
+  * for a workload of n tiles the partitioner (mpdata_fpm_partition) returns
+    k CTAs with x_right tiles and P - k with x_left, or the balanced split;
+  * the speed functions of the available tile shapes are compared and the
+    shape with the shortest predicted step is chosen.
+
+Usage:  python -m paper_1507_01265_gb300.tune --grid 1024 512 64
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+
+import numpy as np
+
+from . import Batch, fpm
+
+TILES = {(32, 24): (32, 24), (32, 16): (32, 16)}
+
+
+def _device_fields(nx, ny, nz, seed=11, periodic=(1, 1, 0)):
+    import torch
+    import gen.fields as F
+    f = F.rotation_blobs(nx=nx, ny=ny, nz=nz, nblobs=2, seed=seed, periodic=periodic)
+    return f, [torch.from_numpy(a).cuda() for a in (f.h, f.psi, f.u1, f.u2, f.u3)]
+
+
+def _time_batch(b, steps, warmup=2):
+    import torch
+    for _ in range(warmup):
+        b.step(2)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    b.step(steps)
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) * 1e-3 / steps
+
+
+def num_sms():
+    import torch
+    return torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+
+
+def speed_function(tile=(32, 24), xs=(1, 2, 3, 4, 5, 6, 7, 8), nz=64, steps=6):
+    """Measured s(x) in cells/s per CTA for x tiles per CTA, all SMs busy."""
+    P = num_sms()
+    tx, ty = tile
+    speeds = []
+    for x in xs:
+        nx, ny = tx * P, ty * x  # P*x tiles: every CTA of the balanced split gets x
+        f, t = _device_fields(nx, ny, nz)
+        with Batch([(nx, ny, nz, (1, 1, 0))], tile=tile) as b:
+            b.set_fields(0, *t)
+            n, ncta = b.work(0)
+            assert n == P * x and ncta == P
+            dt = _time_batch(b, steps)
+        speeds.append(x * tx * ty * nz / dt)
+        del t
+    return np.array(xs, dtype=float), np.array(speeds)
+
+
+def split_for(n_items, ncta, k, xl, xr):
+    """begin[] of a split where the first k CTAs take xr items, the rest xl."""
+    sizes = [int(round(xr))] * k + [int(round(xl))] * (ncta - k)
+    if sum(sizes) != n_items:
+        raise ValueError("split does not cover the work list")
+    return list(np.concatenate([[0], np.cumsum(sizes)]).astype(int))
+
+
+def tune_grid(nx, ny, nz, periodic=(1, 1, 0), steps=10, tiles=((32, 24), (32, 16)), xs_max=10):
+    """Speed functions per tile shape, the partitioner's choice, and measured
+    step times of the balanced and the chosen split on this grid."""
+    P = num_sms()
+    report = {"grid": [nx, ny, nz], "sms": P, "shapes": {}}
+    f, t = _device_fields(nx, ny, nz, periodic=periodic)
+    best = None
+    for tile in tiles:
+        tx, ty = tile
+        ntiles = math.ceil(nx / tx) * math.ceil(ny / ty)
+        xs, ss = speed_function(tile, xs=tuple(range(1, xs_max + 1)), nz=nz)
+        cond2, x_at, x_more = fpm.condition2(xs, ss)
+        k, xl, xr, t_pred = fpm.partition(ntiles, P, 1.0, xs, ss / (tx * ty * nz))
+        with Batch([(nx, ny, nz, periodic)], tile=tile) as b:
+            b.set_fields(0, *t)
+            n, ncta = b.work(0 if periodic[0] and periodic[1] else 1)
+            variant = 0 if periodic[0] and periodic[1] else 1
+            t_bal = _time_batch(b, steps)
+            chosen = b.get_split(variant)
+            if k > 0:
+                chosen = split_for(n, ncta, k, xl, xr)
+                b.set_split(variant, chosen)
+            t_tuned = _time_batch(b, steps)
+        rec = {"tiles": ntiles, "speed_x": xs.tolist(), "speed_cells_per_s": ss.tolist(),
+               "condition2": bool(cond2), "condition2_sizes": [x_at, x_more],
+               "k_right": k, "x_left": xl, "x_right": xr, "predicted_step_s": t_pred,
+               "balanced_step_s": t_bal, "tuned_step_s": t_tuned,
+               "gcell_steps_per_s_balanced": nx * ny * nz / t_bal / 1e9,
+               "gcell_steps_per_s_tuned": nx * ny * nz / t_tuned / 1e9}
+        report["shapes"]["%dx%d" % tile] = rec
+        if best is None or t_pred < best[1]:
+            best = (tile, t_pred)
+    report["chosen_tile"] = list(best[0])
+    return report
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--grid", type=int, nargs=3, default=[1024, 512, 64])
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--xs-max", type=int, default=8)
+    a = ap.parse_args()
+    rep = tune_grid(*a.grid, steps=a.steps, xs_max=a.xs_max)
+    print(json.dumps(rep))
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,87 @@
+"""Batched persistent launches: every grid of a batch gives exactly (bit for
+bit) what mpdata_step gives on that grid alone, whatever the mix of grids,
+the work split between CTAs, odd or even step counts, or graph replay."""
+import numpy as np
+import pytest
+
+import gen.fields as F
+from gpu_helpers import rand_problem, run_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def mp():
+    import __graft_entry__ as g
+    g.build()
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    import paper_1507_01265_gb300 as mp
+    return mp
+
+
+MIX = [  # (nx, ny, nz, periodic): two-column periodic, two-column lid, one-column
+    (64, 40, 12, (1, 1, 1)), (36, 50, 7, (1, 1, 0)), (40, 30, 10, (0, 1, 1)),
+    (37, 23, 11, (1, 1, 1)), (9, 40, 7, (0, 1, 0)), (96, 24, 4, (1, 0, 1)), (4, 3, 2, (1, 1, 1)),
+]
+
+
+def _fields(mp, fs):
+    import torch
+    return [[torch.from_numpy(a).cuda() for a in (f.h, f.psi, f.u1, f.u2, f.u3)] for f in fs]
+
+
+def _batch(mp, fs, tile=(32, 24), nonosc=True):
+    return mp.Batch([(f.nx, f.ny, f.nz, f.periodic) for f in fs], tile=tile, nonoscillatory=nonosc)
+
+
+@pytest.mark.parametrize("nsteps", [1, 4, 5])
+@pytest.mark.parametrize("graph", [False, True])
+@pytest.mark.parametrize("nonosc", [True, False])
+def test_batch_equals_alone(mp, nsteps, graph, nonosc):
+    import torch
+    fs = [rand_problem((nz, ny, nx), seed=i + 40, periodic=per) for i, (nx, ny, nz, per) in enumerate(MIX)]
+    ts = _fields(mp, fs)
+    with _batch(mp, fs, nonosc=nonosc) as b:
+        for i, t in enumerate(ts):
+            b.set_fields(i, *t)
+        b.step(nsteps, graph=graph)
+        b.step(nsteps, graph=graph)  # a second run reuses the cached graph
+        torch.cuda.synchronize()
+    for f, t in zip(fs, ts):
+        alone = run_gpu(f, 2 * nsteps, nonosc=nonosc)
+        assert np.array_equal(t[1].double().cpu().numpy(), alone), f.name
+
+
+def test_uneven_and_degenerate_splits(mp):
+    import torch
+    fs = [F.tracer_grid(nx, ny, nz, c, seed=7 + i, nsteps=3)
+          for i, (nx, ny, nz, c) in enumerate(F.tracer_batch_dims(count=12, seed=77))]
+    ts = _fields(mp, fs)
+    with _batch(mp, fs, tile=(32, 16)) as b:
+        for i, t in enumerate(ts):
+            b.set_fields(i, *t)
+        for v in range(mp.Batch.VARIANTS):
+            n, ncta = b.work(v)
+            if n == 0:
+                continue
+            split = b.get_split(v)
+            assert split[0] == 0 and split[-1] == n and all(a <= c for a, c in zip(split, split[1:]))
+            # every item on CTA 0 except one item on the last CTA, the rest empty
+            b.set_split(v, [0] + [n - 1] * (ncta - 1) + [n])
+        b.step(3)
+        torch.cuda.synchronize()
+    for f, t in zip(fs, ts):
+        assert np.array_equal(t[1].double().cpu().numpy(), run_gpu(f, 3, tile=(32, 16))), f.name
+
+
+def test_bad_split_is_rejected(mp):
+    fs = [rand_problem((4, 8, 32), seed=1)]
+    with _batch(mp, fs) as b:
+        n, ncta = b.work(0)
+        with pytest.raises(mp.MpdataError):
+            b.set_split(0, [0, n + 1])
+        with pytest.raises(mp.MpdataError):
+            b.set_split(0, [1, n])
+        with pytest.raises(mp.MpdataError):
+            b.step(1)  # fields not set
