@@ -20,6 +20,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <deque>
@@ -53,7 +54,7 @@ struct Request {
     mpdata_request req;
     int state = MPDATA_REQ_QUEUED;
     int error = MPDATA_OK;
-    bool cancel = false;
+    std::atomic<bool> cancel{false};
     size_t field_bytes = 0, bytes = 0;
     int remaining = 0;
     int variant = kSingle, ntiles = 0;
@@ -133,31 +134,21 @@ void fail_request(mpdata_server *s, Request *r, int code) {
     free_request_device(s, r);
 }
 
-// Admission of the queue head (lock held).  Returns false if it must wait.
-bool admit_one(mpdata_server *s, Request *r) {
-    if (s->active.size() >= (size_t)s->o.max_active) return false;
-    if (s->admitted_bytes + r->bytes > s->o.hbm_budget_bytes) return false;
-    ++s->admissions;
-    const bool injected = s->o.inject_alloc_failure > 0 &&
-                          s->admissions % (unsigned)s->o.inject_alloc_failure == 0;
+// Allocate and copy in an admitted request (no lock held: only the
+// scheduler thread touches a request between admission and completion).
+int load_request(mpdata_server *s, Request *r, bool injected) {
     cudaError_t e = injected ? cudaErrorMemoryAllocation : cudaSuccess;
     for (int f = 0; f < 6 && e == cudaSuccess; ++f)
         e = cudaMallocAsync((void **)&r->dev[f], r->field_bytes, s->stream);
     if (e != cudaSuccess) {
         cudaGetLastError();
-        fail_request(s, r, MPDATA_ENOMEM);
-        if (r->bytes <= s->reserved_bytes) s->reserved_bytes -= r->bytes;
-        return true;  // handled (failed); move on
+        return MPDATA_ENOMEM;
     }
     const void *src[5] = {r->req.h, r->req.psi, r->req.u1, r->req.u2, r->req.u3};
     float *dst[5] = {r->dev[0], r->dev[1], r->dev[3], r->dev[4], r->dev[5]};
     for (int f = 0; f < 5 && e == cudaSuccess; ++f)
         e = cudaMemcpyAsync(dst[f], src[f], r->field_bytes, cudaMemcpyHostToDevice, s->stream);
-    if (e != cudaSuccess) {
-        fail_request(s, r, MPDATA_ECUDA);
-        if (r->bytes <= s->reserved_bytes) s->reserved_bytes -= r->bytes;
-        return true;
-    }
+    if (e != cudaSuccess) return MPDATA_ECUDA;
     BatchGrid &g = r->bg;
     g.h = r->dev[0];
     g.buf[0] = r->dev[1];
@@ -165,12 +156,7 @@ bool admit_one(mpdata_server *s, Request *r) {
     g.u1 = r->dev[3];
     g.u2 = r->dev[4];
     g.u3 = r->dev[5];
-    s->admitted_bytes += r->bytes;
-    if (r->bytes <= s->reserved_bytes) s->reserved_bytes -= r->bytes;
-    r->state = MPDATA_REQ_RUNNING;
-    r->t_admit = now_s(s->t0);
-    s->active.push_back(r);
-    return true;
+    return MPDATA_OK;
 }
 
 void balanced_split(const std::vector<double> &cost, int ncta, std::vector<int> &begin) {
@@ -187,28 +173,31 @@ void balanced_split(const std::vector<double> &cost, int ncta, std::vector<int> 
     begin[ncta] = n;
 }
 
-// One tick: advance every active request by `chunk` steps (lock held).
-int run_tick(mpdata_server *s, int chunk) {
+// One tick over `act` (no lock held): upload the work list, launch `chunk`
+// steps, and for requests that finish (or are cancelled) queue the copy-out,
+// the frees and the completion event.  Returns a CUDA error or success.
+cudaError_t run_tick(mpdata_server *s, const std::vector<Request *> &act, int chunk,
+                     std::vector<char> &finished) {
     TickBuffers &T = s->tick[s->tick_index & 1];
+    cudaError_t e = cudaSuccess;
     if (T.in_flight) {
-        cudaError_t e = cudaEventSynchronize(T.ev);
-        if (e != cudaSuccess) return MPDATA_ECUDA;
+        e = cudaEventSynchronize(T.ev);  // keep at most two ticks in flight
+        if (e != cudaSuccess) return e;
         T.in_flight = false;
     }
-    const int na = (int)s->active.size();
+    const int na = (int)act.size();
     T.h_grids.resize(na);
     T.h_items.clear();
-    T.h_begin.clear();
-    int voff[kNumVariants + 1] = {0, 0, 0, 0};
+    int voff[kNumVariants] = {0, 0, 0};
     std::vector<double> cost[kNumVariants];
     std::vector<int2> items[kNumVariants];
     for (int a = 0; a < na; ++a) {
-        Request *r = s->active[a];
+        Request *r = act[a];
         T.h_grids[a] = r->bg;
-        const int tx = r->variant == kSingle ? 32 : 32, ty = r->variant == kSingle ? 16 : s->o.tile_y;
+        const int ty = r->variant == kSingle ? 16 : s->o.tile_y;
         for (int t = 0; t < r->ntiles; ++t) {
             items[r->variant].push_back(make_int2(a, t));
-            cost[r->variant].push_back((double)tx * ty * (r->bg.g.nz + 3));
+            cost[r->variant].push_back(32.0 * ty * (r->bg.g.nz + 3));
         }
     }
     int ncta[kNumVariants];
@@ -227,7 +216,7 @@ int run_tick(mpdata_server *s, int chunk) {
         item_base += (int)items[v].size();
     }
     T.h_begin = begin_all;
-    cudaError_t e = ensure(&T.d_grids, &T.cap_grids, (size_t)na, s->stream);
+    e = ensure(&T.d_grids, &T.cap_grids, (size_t)na, s->stream);
     if (e == cudaSuccess) e = ensure(&T.d_items, &T.cap_items, T.h_items.size(), s->stream);
     if (e == cudaSuccess) e = ensure(&T.d_begin, &T.cap_begin, T.h_begin.size(), s->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(T.d_grids, T.h_grids.data(), sizeof(BatchGrid) * na, cudaMemcpyHostToDevice, s->stream);
@@ -249,46 +238,26 @@ int run_tick(mpdata_server *s, int chunk) {
         }
     }
     if (e == cudaSuccess) e = cudaEventRecord(T.ev, s->stream);
-    if (e != cudaSuccess) {
-        for (Request *r : s->active) {
-            fail_request(s, r, MPDATA_ECUDA);
-            s->admitted_bytes -= r->bytes;
-        }
-        s->active.clear();
-        s->cv_done.notify_all();
-        return MPDATA_ECUDA;
-    }
+    if (e != cudaSuccess) return e;
     T.in_flight = true;
     s->tick_index++;
-    // bookkeeping: buffer parity, finished requests
-    std::vector<Request *> still;
-    for (Request *r : s->active) {
+    finished.assign(na, 0);
+    for (int a = 0; a < na && e == cudaSuccess; ++a) {
+        Request *r = act[a];
         r->remaining -= chunk;
-        s->cell_steps += (double)r->req.nx * r->req.ny * r->req.nz * chunk;
         if (chunk & 1) std::swap(r->bg.buf[0], r->bg.buf[1]);
-        if (r->remaining <= 0 || r->cancel) {
-            if (r->cancel) {
-                r->state = MPDATA_REQ_CANCELLED;
-                r->t_done = now_s(s->t0);
-                free_request_device(s, r);
-                cudaEventRecord(r->done_ev, s->stream);
-                s->copying.push_back(r);  // release its budget once the stream passes this point
-                continue;
-            }
-            cudaError_t c = cudaMemcpyAsync(r->req.psi, r->bg.buf[0], r->field_bytes, cudaMemcpyDeviceToHost, s->stream);
-            if (c == cudaSuccess) c = cudaEventRecord(r->done_ev, s->stream);
-            if (c != cudaSuccess) { fail_request(s, r, MPDATA_ECUDA); s->admitted_bytes -= r->bytes; continue; }
-            free_request_device(s, r);
-            s->copying.push_back(r);
-        } else {
-            still.push_back(r);
-        }
+        const bool cancel = r->cancel.load();
+        if (r->remaining > 0 && !cancel) continue;
+        finished[a] = cancel ? 2 : 1;
+        if (!cancel)
+            e = cudaMemcpyAsync(r->req.psi, r->bg.buf[0], r->field_bytes, cudaMemcpyDeviceToHost, s->stream);
+        free_request_device(s, r);
+        if (e == cudaSuccess) e = cudaEventRecord(r->done_ev, s->stream);
     }
-    s->active.swap(still);
-    return MPDATA_OK;
+    return e;
 }
 
-void finish_copies(mpdata_server *s) {
+void finish_copies(mpdata_server *s) {  // lock held
     std::vector<Request *> still;
     bool any = false;
     for (Request *r : s->copying) {
@@ -303,8 +272,8 @@ void finish_copies(mpdata_server *s) {
                 r->state = MPDATA_REQ_FAILED;
                 r->error = MPDATA_ECUDA;
             }
-            r->t_done = now_s(s->t0);
         }
+        r->t_done = now_s(s->t0);
         any = true;
     }
     s->copying.swap(still);
@@ -313,44 +282,99 @@ void finish_copies(mpdata_server *s) {
 
 void scheduler(mpdata_server *s) {
     cudaSetDevice(s->device);
-    std::unique_lock<std::mutex> lk(s->mu);
+    std::vector<Request *> act, admit;
+    std::vector<char> admit_injected, finished;
     for (;;) {
-        finish_copies(s);
-        // cancelled queue entries
-        for (auto it = s->queue.begin(); it != s->queue.end();) {
-            if ((*it)->cancel) {
-                (*it)->state = MPDATA_REQ_CANCELLED;
-                (*it)->t_done = now_s(s->t0);
-                if ((*it)->bytes <= s->reserved_bytes) s->reserved_bytes -= (*it)->bytes;
-                it = s->queue.erase(it);
-                s->cv_done.notify_all();
-            } else {
-                ++it;
+        admit.clear();
+        admit_injected.clear();
+        {
+            std::unique_lock<std::mutex> lk(s->mu);
+            finish_copies(s);
+            for (auto it = s->queue.begin(); it != s->queue.end();) {  // cancelled while queued
+                Request *r = *it;
+                if (r->cancel.load()) {
+                    r->state = MPDATA_REQ_CANCELLED;
+                    r->t_done = now_s(s->t0);
+                    if (r->bytes <= s->reserved_bytes) s->reserved_bytes -= r->bytes;
+                    it = s->queue.erase(it);
+                    s->cv_done.notify_all();
+                } else {
+                    ++it;
+                }
             }
-        }
-        while (!s->queue.empty() && !s->stop) {
-            Request *r = s->queue.front();
-            if (!admit_one(s, r)) break;
-            s->queue.pop_front();
-            if (r->state == MPDATA_REQ_FAILED) s->cv_done.notify_all();
-        }
-        if (s->active.empty()) {
-            if (s->stop && s->copying.empty()) break;
-            if (!s->copying.empty()) {
-                lk.unlock();
-                std::this_thread::sleep_for(std::chrono::microseconds(50));
-                lk.lock();
-            } else {
-                s->cv_work.wait_for(lk, std::chrono::milliseconds(5));
+            // admission: FIFO while the budget and the slots allow
+            while (!s->stop && !s->queue.empty()) {
+                Request *r = s->queue.front();
+                if (s->active.size() + admit.size() >= (size_t)s->o.max_active) break;
+                if (s->admitted_bytes + r->bytes > s->o.hbm_budget_bytes) break;
+                s->queue.pop_front();
+                s->admitted_bytes += r->bytes;
+                if (r->bytes <= s->reserved_bytes) s->reserved_bytes -= r->bytes;
+                ++s->admissions;
+                admit.push_back(r);
+                admit_injected.push_back(s->o.inject_alloc_failure > 0 &&
+                                         s->admissions % (unsigned)s->o.inject_alloc_failure == 0);
             }
-            continue;
+            if (s->active.empty() && admit.empty()) {
+                if (s->stop && s->copying.empty()) break;
+                if (!s->copying.empty()) {
+                    lk.unlock();
+                    std::this_thread::sleep_for(std::chrono::microseconds(50));
+                } else {
+                    s->cv_work.wait_for(lk, std::chrono::milliseconds(5));
+                }
+                continue;
+            }
+            if (s->stop)
+                for (Request *r : s->active) r->cancel.store(true);
         }
-        if (s->stop) {
-            for (Request *r : s->active) r->cancel = true;
+        // copy-in of the admitted requests (no lock)
+        std::vector<int> load_rc(admit.size());
+        for (size_t i = 0; i < admit.size(); ++i) load_rc[i] = load_request(s, admit[i], admit_injected[i]);
+        {
+            std::lock_guard<std::mutex> lk(s->mu);
+            for (size_t i = 0; i < admit.size(); ++i) {
+                Request *r = admit[i];
+                if (load_rc[i] != MPDATA_OK) {
+                    fail_request(s, r, load_rc[i]);
+                    s->admitted_bytes -= r->bytes;
+                    s->cv_done.notify_all();
+                    continue;
+                }
+                r->state = MPDATA_REQ_RUNNING;
+                r->t_admit = now_s(s->t0);
+                s->active.push_back(r);
+            }
+            act = s->active;
         }
+        if (act.empty()) continue;
         int chunk = s->o.chunk_steps;
-        for (Request *r : s->active) chunk = std::min(chunk, std::max(r->remaining, 1));
-        run_tick(s, chunk);
+        for (Request *r : act) chunk = std::min(chunk, std::max(r->remaining, 1));
+        cudaError_t e = run_tick(s, act, chunk, finished);  // no lock
+        {
+            std::lock_guard<std::mutex> lk(s->mu);
+            std::vector<Request *> still;
+            for (size_t a = 0; a < act.size(); ++a) {
+                Request *r = act[a];
+                if (e != cudaSuccess) {
+                    fail_request(s, r, MPDATA_ECUDA);
+                    s->admitted_bytes -= r->bytes;
+                    continue;
+                }
+                s->cell_steps += (double)r->req.nx * r->req.ny * r->req.nz * chunk;
+                if (finished[a]) {
+                    if (finished[a] == 2) r->state = MPDATA_REQ_CANCELLED;
+                    s->copying.push_back(r);
+                } else {
+                    still.push_back(r);
+                }
+            }
+            s->active.swap(still);
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                s->cv_done.notify_all();
+            }
+        }
     }
     cudaStreamSynchronize(s->stream);
 }
@@ -487,7 +511,7 @@ int mpdata_cancel(mpdata_server_t *s, uint64_t ticket) {
     std::lock_guard<std::mutex> lk(s->mu);
     auto it = s->all.find(ticket);
     if (it == s->all.end()) return sfail(MPDATA_ENOENT, "unknown ticket %llu", (unsigned long long)ticket);
-    it->second->cancel = true;
+    it->second->cancel.store(true);
     s->cv_work.notify_one();
     return MPDATA_OK;
 }

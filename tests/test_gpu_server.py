@@ -64,11 +64,12 @@ def test_results_equal_alone_in_the_mix(mp):
 
 
 def test_budget_refusal_timeout_cancel(mp):
-    f = F.rotation_blobs(nx=64, ny=64, nz=16, nsteps=400, seed=3)
+    f = F.rotation_blobs(nx=64, ny=64, nz=16, seed=3)
     need = 6 * f.ncells * 4
     with mp.Server(hbm_budget_bytes=need, max_queued=0, chunk_steps=2) as srv:
         a = f.psi.copy()
-        ta = srv.submit(f.h, a, f.u1, f.u2, f.u3, 400, periodic=f.periodic)
+        # long enough (several seconds) to still be resident for the checks below
+        ta = srv.submit(f.h, a, f.u1, f.u2, f.u3, 200000, periodic=f.periodic)
         with pytest.raises(mp.MpdataError) as e:  # budget reserved by the first request
             srv.submit(f.h, f.psi.copy(), f.u1, f.u2, f.u3, 1, periodic=f.periodic)
         assert e.value.code == mp._lib.MPDATA_EBUSY
