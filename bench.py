@@ -51,6 +51,11 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
+    ap.add_argument("--workload", default="grid", choices=["grid", "tracers", "serve"],
+                    help="grid: 1024x512x64 (default); tracers: 64 uneven grids batched; "
+                         "serve: Poisson arrivals through the serving runtime vs one solve per launch")
+    ap.add_argument("--serve-seconds", type=float, default=10.0)
+    ap.add_argument("--serve-rate", type=float, default=200.0)
     return ap.parse_args()
 
 
@@ -200,11 +205,174 @@ def run_reference(args, rank, world):
     return 0
 
 
+def run_tracers(args):
+    """64 independent tracer grids (nx, ny log-uniform in [32, 512], nz in
+    [16, 64], constant Courant vectors), 20 steps each: one persistent,
+    graph-captured batched launch per step vs one launch per grid."""
+    import torch
+    import gen.fields as F
+    import paper_1507_01265_gb300 as mp
+    dims = F.tracer_batch_dims(count=64, seed=1510)
+    fs = [F.tracer_grid(nx, ny, nz, c, seed=2000 + i) for i, (nx, ny, nz, c) in enumerate(dims)]
+    ts = [[torch.from_numpy(a).cuda() for a in (f.h, f.psi, f.u1, f.u2, f.u3)] for f in fs]
+    cells = sum(f.ncells for f in fs)
+    nsteps = 20
+    stream = torch.cuda.current_stream()
+    res = {}
+    with mp.Batch([(f.nx, f.ny, f.nz, f.periodic) for f in fs]) as b:
+        for i, t in enumerate(ts):
+            b.set_fields(i, *t)
+        for _ in range(args.warmup):
+            b.step(nsteps, graph=True)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            b.step(nsteps, graph=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        res["batched"] = e0.elapsed_time(e1) / args.steps
+    solvers = [mp.Solver(f.nx, f.ny, f.nz, periodic=f.periodic) for f in fs]
+    for _ in range(args.warmup):
+        for s_, t in zip(solvers, ts):
+            s_.step(*t, nsteps)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        for s_, t in zip(solvers, ts):
+            s_.step(*t, nsteps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    res["per_grid"] = e0.elapsed_time(e1) / args.steps
+    for s_ in solvers:
+        s_.close()
+    v = cells * nsteps / (res["batched"] * 1e-3) / 1e9
+    line = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": res["batched"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "64 tracer grids, nx/ny log-uniform [32,512], nz [16,64], 20 steps; "
+                                   "persistent batched launch captured in a CUDA graph",
+                       "cells": cells, "mpdata_steps_per_step": nsteps},
+            "per_grid_launches": {"value": cells * nsteps / (res["per_grid"] * 1e-3) / 1e9,
+                                  "ms_per_step": res["per_grid"]},
+            "speedup_vs_per_grid": res["per_grid"] / res["batched"]}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def serve_requests(rate, seconds, seed=1511):
+    """Poisson arrival times and per-request (template, nsteps): dims
+    log-uniform from 32^3 to 512x256x64, nsteps U[10, 200], rotation field
+    max |C| U[0.1, 0.5], blob psi.  Fields come from a pool of 48 seeded
+    templates so that generation stays off the clock."""
+    import gen.fields as F
+    st = F.Stream(seed)
+    templates = []
+    for i in range(48):
+        nx = st.log_uniform_int(32, 512)
+        ny = st.log_uniform_int(32, 256)
+        nz = st.log_uniform_int(32, 64)
+        templates.append(F.rotation_blobs(nx=nx, ny=ny, nz=nz, max_c=st.scalar(0.1, 0.5), nblobs=2,
+                                          seed=3000 + i, periodic=(1, 1, 0)))
+    t, reqs = 0.0, []
+    while True:
+        t += -math.log(1.0 - st.scalar()) / rate
+        if t > seconds:
+            break
+        reqs.append((t, int(st.scalar(0, len(templates))), int(st.scalar(10, 201))))
+    return templates, reqs
+
+
+def run_serve(args):
+    """Served (continuous batching) vs plain (one solve per launch, in arrival
+    order): throughput and p50/p99 latency under the same arrivals."""
+    import threading
+    import numpy as np
+    import torch
+    import paper_1507_01265_gb300 as mp
+    templates, reqs = serve_requests(args.serve_rate, args.serve_seconds)
+    pin = lambda a: torch.from_numpy(a).pin_memory()
+    tmpl = [(pin(f.h), f.psi, pin(f.u1), pin(f.u2), pin(f.u3)) for f in templates]
+    outs = [pin(templates[k].psi.copy()) for _, k, _ in reqs]
+    work = sum(templates[k].ncells * n for _, k, n in reqs)
+
+    def percentile(lat):
+        a = np.sort(np.array(lat))
+        return float(np.percentile(a, 50)), float(np.percentile(a, 99))
+
+    # served
+    srv = mp.Server(hbm_budget_bytes=120 << 30, chunk_steps=8)
+    tickets = [None] * len(reqs)
+    t0 = time.perf_counter()
+
+    def submitter():
+        for i, (ta, k, n) in enumerate(reqs):
+            d = t0 + ta - time.perf_counter()
+            if d > 0:
+                time.sleep(d)
+            h, _, u1, u2, u3 = tmpl[k]
+            tickets[i] = (time.perf_counter(), srv.submit(h, outs[i], u1, u2, u3, n, periodic=(1, 1, 0)))
+    th = threading.Thread(target=submitter)
+    th.start()
+    lat = []
+    for i in range(len(reqs)):
+        while tickets[i] is None:
+            time.sleep(0.0005)
+        ts_, tk = tickets[i]
+        srv.wait(tk)
+        t_sub, t_adm, t_done = srv.times(tk)
+        lat.append(t_done - t_sub)
+    th.join()
+    t_end = max(srv.times(tk)[2] for _, tk in tickets)
+    t_first = min(srv.times(tk)[0] for _, tk in tickets)
+    served = {"gcell_steps_per_s": work / (t_end - t_first) / 1e9, "requests": len(reqs)}
+    served["p50_s"], served["p99_s"] = percentile(lat)
+    srv.close()
+    # plain: one solve per launch, in arrival order
+    solvers = {}
+    lat2 = []
+    t0 = time.perf_counter()
+    t_free = 0.0
+    for i, (ta, k, n) in enumerate(reqs):
+        d = t0 + ta - time.perf_counter()
+        if d > 0:
+            time.sleep(d)
+        f = templates[k]
+        key = (f.nx, f.ny, f.nz)
+        if key not in solvers:
+            solvers[key] = mp.Solver(f.nx, f.ny, f.nz, periodic=(1, 1, 0))
+        h, _, u1, u2, u3 = tmpl[k]
+        outs[i].copy_(torch.from_numpy(f.psi))
+        solvers[key].solve_host(h, outs[i], u1, u2, u3, n)
+        lat2.append(time.perf_counter() - (t0 + ta))
+    t_plain = time.perf_counter() - t0 - reqs[0][0]
+    for s_ in solvers.values():
+        s_.close()
+    plain = {"gcell_steps_per_s": work / t_plain / 1e9}
+    plain["p50_s"], plain["p99_s"] = percentile(lat2)
+    line = {"metric": METRIC, "value": served["gcell_steps_per_s"], "unit": UNIT, "n_gpus": 1,
+            "steps": len(reqs), "warmup": 0, "ms_per_step": None, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "serving: Poisson arrivals %.0f req/s for %.0f s, dims log-uniform "
+                                   "32^3..512x256x64, nsteps U[10,200], 120 GB budget"
+                                   % (args.serve_rate, args.serve_seconds),
+                       "offered_gcell_steps_per_s": work / args.serve_seconds / 1e9},
+            "served": served, "plain_one_solve_per_launch": plain,
+            "throughput_ratio": served["gcell_steps_per_s"] / plain["gcell_steps_per_s"]}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     rank, world, local, dist = dist_init(args)
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.workload == "tracers":
+        return run_tracers(args) if rank == 0 else 0
+    if args.workload == "serve":
+        return run_serve(args) if rank == 0 else 0
 
     import numpy as np
     import torch
