@@ -72,6 +72,16 @@ def dist_init(args):
     return rank, world, local, pg
 
 
+def max_over_ranks(x, dist, device=None):
+    """Largest value of x over all ranks (x itself without a process group)."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -406,11 +416,7 @@ def main():
             solver.step(h, psi, u1, u2, u3, NSTEPS, stream)
         ev1.record(stream)
         barrier()
-    ms = ev0.elapsed_time(ev1)
-    if dist is not None:
-        tt = torch.tensor([ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
+    ms = max_over_ranks(ev0.elapsed_time(ev1), dist, dev)
     ms_per_step = ms / args.steps
     launches = args.steps * NSTEPS
     value = world * ncells * NSTEPS * args.steps / (ms * 1e-3) / 1e9
@@ -435,11 +441,7 @@ def main():
         t0 = time.perf_counter()
         for _ in range(args.e2e_steps):
             solver.solve_host(hh, hp, h1, h2, h3, NSTEPS, stream)
-        dt = time.perf_counter() - t0
-        if dist is not None:
-            tt = torch.tensor([dt], device=dev)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            dt = float(tt.item())
+        dt = max_over_ranks(time.perf_counter() - t0, dist, dev)
         e2e = {"value": world * ncells * NSTEPS * args.e2e_steps / dt / 1e9, "unit": UNIT,
                "h2d_bytes_per_step": 5 * 4 * ncells, "d2h_bytes_per_step": 4 * ncells,
                "steps": args.e2e_steps}
