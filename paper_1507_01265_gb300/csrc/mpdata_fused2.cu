@@ -98,8 +98,10 @@ struct Lay2 {
     static constexpr int CPR = EX / 4;          // 16-byte chunks per plane row
     static constexpr int NCH = CPR * EY;
     static_assert(NCH <= NT, "one load chunk per thread");
-    static constexpr int RING = 0, P1 = 20, SX = 22, SY = 24, SZ = 26;
-    static constexpr int V1 = 27, V2 = 28, BU = 29, BD = 30, GX = 31, GY = 32, NPLANES = 33;
+    static constexpr int NR = 5;                // input ring depth: planes p-2 .. p+2
+    static constexpr int RING = 0, P1 = 5 * NR, SX = P1 + 2, SY = SX + 2, SZ = SY + 2;
+    static constexpr int V1 = SZ + 1, V2 = V1 + 1, BU = V2 + 1, BD = BU + 1, GX = BD + 1, GY = GX + 1;
+    static constexpr int NPLANES = GY + 1;
 };
 
 // Pair (px, row) of thread t; pair px covers columns 2px-4, 2px-3 of the tile.
@@ -123,6 +125,11 @@ __device__ __forceinline__ void onion2(int t, int &px, int &ry) {
     t -= HX + 2;
     px = 1 + t;
     ry = -2;
+}
+
+__device__ __forceinline__ int slot5(int q) {
+    const int r = q % 5;
+    return r < 0 ? r + 5 : r;
 }
 
 __device__ __forceinline__ int wrap(int a, int n) {
@@ -172,7 +179,7 @@ __device__ __forceinline__ void pairs_tile(const TileArgs &a, int tile, float *s
     const int ntx = a.ntx;
     constexpr int EX = L::EX, PL = L::PL;
     constexpr int PB = PL * 4;         // bytes per plane
-    constexpr int FB = 4 * PB;         // bytes between ring fields
+    constexpr int FB = L::NR * PB;     // bytes between ring fields
     constexpr int RB = EX * 4;         // bytes per plane row
     // plane offsets (bytes) of the non-ring planes
     constexpr int oP1 = L::P1 * PB, oSX = L::SX * PB, oSY = L::SY * PB, oSZ = L::SZ * PB;
@@ -237,7 +244,7 @@ __device__ __forceinline__ void pairs_tile(const TileArgs &a, int tile, float *s
         if (has_chunk) {
             const long long pc = (long long)(perz ? wrap(p, nz) : min(max(p, 0), nz - 1)) * nxy + ld_off;
             const bool zz = !perz && (p <= 0 || p >= nz);  // z-lid face
-            const unsigned d = ld_dst + (unsigned)((p & 3) * PB);
+            const unsigned d = ld_dst + (unsigned)(slot5(p) * PB);
             cp16(d, psi + pc, z_all);
             cp16(d + FB, u1 + pc, z_all);
             cp16(d + 2 * FB, u2 + pc, z_u2);
@@ -254,54 +261,46 @@ __device__ __forceinline__ void pairs_tile(const TileArgs &a, int tile, float *s
     const int wlo = perz ? -2 : 0, whi = perz ? nz : nz - 2;
     const int vlo = perz ? -1 : 0, vhi = perz ? nz : nz - 1;
 
+    // Schedule of iteration p (q1 = p-1, q2 = p-2, q3 = p-3), three barriers:
+    //   alpha: x/y divergence of q3 from neighbour fluxes | pair sums at q1 |
+    //          x/y pseudo-velocities at q2                               -> F
+    //   beta:  z-face pseudo-velocity above q2, extrema and limiter factors
+    //          at q2; wait for the loads of plane p+1                    -> H
+    //   gamma: limited corrective fluxes at q2, output of q3, donor pass
+    //          of plane p (one plane ahead, filling the warps that the
+    //          flux stage leaves idle)                                   -> X
+    // Inputs load two planes ahead into a 5-plane ring, so planes p-2 .. p+1
+    // stay readable for the whole iteration while p+2 streams in.
     const F2 Z = bc(0.f);
     F2 pn_mm = Z, pn_m = Z, pn_c = Z;     // psi^n at q2-1, q2, q1
-    F2 p1a = Z, p1b = Z;                  // psi1 at q2-1, q2
+    F2 p1a = Z, p1b = Z, p1c = Z;         // psi1 at q2-1, q2, q1
+    F2 u1b = Z, u2b = Z, u3b = Z, hb = bc(1.f);   // own inputs at q2
+    F2 u1c = Z, u2c = Z, u3c = Z, hc = bc(1.f);   // own inputs at q1
     F2 sxa = Z, sxb = Z, sya = Z, syb = Z;
-    F2 u1b = Z, u2b = Z, u3b = Z, hb = bc(1.f), u3c = Z;
     F2 wlo_v = Z, bu_prev = Z, bd_prev = Z, h_prev = bc(1.f);
     F2 dacc = Z, gx_own = Z, gy_own = Z;
 
     issue(p_first);
+    issue(p_first + 1);
     for (int p = p_first; p <= p_last; ++p) {
         const int q1 = p - 1, q2 = p - 2, q3 = p - 3;
-        if (p + 1 <= p_last) issue(p + 1);
+        if (p + 2 <= p_last) issue(p + 2);
         else asm volatile("cp.async.commit_group;\n" ::: "memory");
-        asm volatile("cp.async.wait_group 1;\n" ::: "memory");
-        if (LID && patch_u1) sm[(ld_dst - sm_base) / 4u + (unsigned)(L::RING * PL + 4 * PL + (p & 3) * PL)] = 0.f;
-        __syncthreads();  // (A)
 
         // slot bases of this iteration
-        const unsigned rp = tb + (unsigned)((p & 3) * PB);    // ring, plane p
-        const unsigned r1 = tb + (unsigned)((q1 & 3) * PB);   // ring, plane q1
-        const unsigned r2 = tb + (unsigned)((q2 & 3) * PB);   // ring, plane q2
-        const unsigned b1 = tb + (unsigned)((q1 & 1) * PB);   // psi1/SX/SY slot of q1
-        const unsigned b2 = tb + (unsigned)((q2 & 1) * PB);   // psi1/SX/SY slot of q2
+        const unsigned r2 = tb + (unsigned)(slot5(q2) * PB);    // ring, plane q2
+        const unsigned r1 = tb + (unsigned)(slot5(q1) * PB);    // ring, plane q1
+        const unsigned rp = tb + (unsigned)(slot5(p) * PB);     // ring, plane p
+        const unsigned rp1 = tb + (unsigned)(slot5(p + 1) * PB);  // ring, plane p+1
+        const unsigned b1 = tb + (unsigned)((q1 & 1) * PB);     // psi1/SX/SY slot of q1
+        const unsigned b2 = tb + (unsigned)((q2 & 1) * PB);     // psi1/SX/SY slot of q2 (= p)
 
+
+        // ---- alpha ----
         if (in_out && q3 >= 0 && q3 <= nz - 1) {
             const F2 gxr = rshF(tb + oGX, gx_own), gyu = ldp<oGY + RB>(tb);
             dacc = add(add(sub(gxr, gx_own), sub(gyu, gy_own)), dacc);
         }
-
-        // (a1) donor pass at q1
-        const F2 pn_p = ldp<0>(rp);
-        const F2 u3p = ldp<3 * FB>(rp);
-        const F2 u1c = ldp<FB>(r1), u2c = ldp<2 * FB>(r1), hc = ldp<4 * FB>(r1);
-        F2 p1c = p1b;
-        if (q1 >= q1lo && q1 <= q1hi) {
-            const F2 fxl = flux(u1c, lshC(r1, pn_c), pn_c);
-            const F2 fxh = flux(rshF(r1 + FB, u1c), pn_c, rshC(r1, pn_c));
-            const F2 fyl = flux(u2c, ldD(r1), pn_c);
-            const F2 fyh = flux(ldp<2 * FB + RB>(r1), pn_c, ldU(r1));
-            const F2 fzl = flux(u3c, pn_m, pn_c);
-            const F2 fzh = flux(u3p, pn_c, pn_p);
-            const F2 div = add(add(sub(fxh, fxl), sub(fyh, fyl)), sub(fzh, fzl));
-            p1c = sub(pn_c, mul(div, rcp(hc)));
-        }
-        if (q1 >= q1lo && q1 <= q1top) stp<oP1>(b1, p1c);
-        __syncthreads();  // (D)
-
-        // (a2) pair sums (all threads) and x/y pseudo-velocities at q2
         F2 sxc = sxb, syc = syb, v1_own = Z, v2_own = Z, pl = Z, pd = Z;
         if (q1 >= q1lo && q1 <= q1top) {
             sxc = add(lshC(b1 + oP1, p1c), p1c);
@@ -337,7 +336,7 @@ __device__ __forceinline__ void pairs_tile(const TileArgs &a, int tile, float *s
         }
         __syncthreads();  // (F)
 
-        // (a2) z-face above q2, (a3)+(a4) extrema and limiter factors at q2
+        // ---- beta ----
         F2 whi_v = Z, bu_c = Z, bd_c = Z;
         if (in_beta) {
             if (q2 >= wlo && q2 <= whi) {
@@ -367,9 +366,11 @@ __device__ __forceinline__ void pairs_tile(const TileArgs &a, int tile, float *s
                 stp<oBD>(tb, bd_c);
             }
         }
+        asm volatile("cp.async.wait_group 1;\n" ::: "memory");  // plane p+1 landed
+        if (LID && patch_u1) sm[(ld_dst - sm_base) / 4u + (unsigned)(L::RING * PL + L::NR * PL + slot5(p + 1) * PL)] = 0.f;
         __syncthreads();  // (H)
 
-        // (a5)+(a6) limited corrective fluxes at q2, output of q3
+        // ---- gamma ----
         if (in_vm && q2 >= 0 && q2 <= nz - 1) {
             F2 vm1 = v1_own, vm2 = v2_own;
             if (NONOSC) {
@@ -402,12 +403,31 @@ __device__ __forceinline__ void pairs_tile(const TileArgs &a, int tile, float *s
             if (q3ok && store) st2(outp + (long long)q3 * nxy, sub(p1a, mul(add(dacc, gz), rcp(h_prev))));
             dacc = sub(Z, gz);
         }
+        // (a1) donor pass at plane p (psi^n at p-1, p, p+1)
+        F2 p1n = p1c;  // lid top ghost: zero-gradient copy of the plane below
+        const F2 pn_p = ldp<0>(rp);
+        const F2 u1p = ldp<FB>(rp), u2p = ldp<2 * FB>(rp), u3p = ldp<3 * FB>(rp), hp = ldp<4 * FB>(rp);
+        if (p >= q1lo && p <= q1hi) {
+            const F2 pn_n = ldp<0>(rp1);
+            const F2 u3n = ldp<3 * FB>(rp1);
+            const F2 fxl = flux(u1p, lshC(rp, pn_p), pn_p);
+            const F2 fxh = flux(rshF(rp + FB, u1p), pn_p, rshC(rp, pn_p));
+            const F2 fyl = flux(u2p, ldD(rp), pn_p);
+            const F2 fyh = flux(ldp<2 * FB + RB>(rp), pn_p, ldU(rp));
+            const F2 fzl = flux(u3p, pn_c, pn_p);
+            const F2 fzh = flux(u3n, pn_p, pn_n);
+            const F2 div = add(add(sub(fxh, fxl), sub(fyh, fyl)), sub(fzh, fzl));
+            p1n = sub(pn_p, mul(div, rcp(hp)));
+        }
+        if (p >= q1lo && p <= q1top) stp<oP1>(b2, p1n);  // slot of p == slot of q2 (no longer read)
+        __syncthreads();  // (X)
 
         h_prev = hb;
         pn_mm = pn_m; pn_m = pn_c; pn_c = pn_p;
-        p1a = p1b; p1b = p1c;
+        u1b = u1c; u2b = u2c; u3b = u3c; hb = hc;
+        u1c = u1p; u2c = u2p; u3c = u3p; hc = hp;
+        p1a = p1b; p1b = p1c; p1c = p1n;
         sxa = sxb; sxb = sxc; sya = syb; syb = syc;
-        u1b = u1c; u2b = u2c; u3b = u3c; u3c = u3p; hb = hc;
         wlo_v = whi_v; bu_prev = bu_c; bd_prev = bd_c;
     }
     asm volatile("cp.async.wait_all;\n" ::: "memory");
