@@ -282,6 +282,7 @@ __device__ __forceinline__ void pairs_tile(const TileArgs &a, int tile, float *s
 
     issue(p_first);
     issue(p_first + 1);
+#pragma unroll 2
     for (int p = p_first; p <= p_last; ++p) {
         const int q1 = p - 1, q2 = p - 2, q3 = p - 3;
         if (p + 2 <= p_last) issue(p + 2);
