@@ -18,6 +18,14 @@
  *   (a5) limited velocities                   -> Vmon
  *   (a6) corrective donor-cell pass           -> psi^{n+1}
  *
+ * With iterations = 3 stages (a2)-(a6) run a second time on the result of
+ * the first corrective pass, the pseudo-velocities now built from the
+ * limited velocities that pass used in place of the Courant numbers (each
+ * corrective pass estimates the error of the pass before it, Smolarkiewicz
+ * 1984 §3).  Parity unpinned: under the limiter, that the second pass is
+ * built from the limited (not the raw) velocities of the first is a
+ * reading; no pin separates the two (they coincide without the limiter).
+ *
  * The formulas follow the published MPDATA scheme: the basic two-pass scheme
  * with its cross terms (Smolarkiewicz 1984, J. Comput. Phys. 54), the
  * nonoscillatory option (Smolarkiewicz & Grabowski 1990, J. Comput. Phys. 86)
@@ -36,21 +44,32 @@
  *     edge cell (used by the cross terms and the extrema);
  *   - h-bar on a face is the mean of the two adjacent h;
  *   - eps is added to every A, B and beta denominator;
- *   - the extrema are taken over both psi^n and psi1.
+ *   - the extrema of a corrective pass are taken over psi^n and the field
+ *     that pass corrects (psi1 for the first one), or, with extrema = 1,
+ *     over the corrected field alone.
+ *
+ * An OpenMP build of this same file (-fopenmp) runs the per-cell loops on
+ * all host cores; every cell is computed by the same expression as in the
+ * serial build, so the two builds return identical bits.
  */
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 typedef struct {
     int nx, ny, nz;
     int periodic[3];     /* per axis: 1 periodic, 0 rigid lid */
-    int iterations;      /* 1: donor cell only; 2: one corrective pass */
+    int iterations;      /* 1: donor cell only; 2, 3: one or two corrective passes */
     int nonoscillatory;  /* 1: apply the beta limiter to the antidiffusive velocities */
     double eps;          /* > 0 */
+    int extrema;         /* 0: psi^n and the corrected field; 1: the corrected field only */
 } oracle_cfg;
 
-/* Optional intermediate outputs (any pointer may be NULL). */
+/* Optional intermediate outputs of the first corrective pass (any pointer
+ * may be NULL). */
 typedef struct {
     double *psi1;
     double *v1, *v2, *v3;
@@ -117,6 +136,7 @@ static double upstream_flux(double U, double L, double R)
 static void donor_pass(const oracle_cfg *c, const double *h, const double *psi,
                        const double *w1, const double *w2, const double *w3, double *out)
 {
+#pragma omp parallel for collapse(2) schedule(static)
     for (int k = 0; k < c->nz; ++k)
         for (int j = 0; j < c->ny; ++j)
             for (int i = 0; i < c->nx; ++i) {
@@ -133,8 +153,9 @@ static void donor_pass(const oracle_cfg *c, const double *h, const double *psi,
 }
 
 /* (a2): antidiffusive pseudo-velocity on the lower face (along `axis`) of
- * cell (i,j,k).  With e the unit step along `axis` and a, b the two other
- * axes:
+ * cell (i,j,k), for the field psi1 being corrected and the face velocities
+ * u of the pass that made it.  With e the unit step along `axis` and a, b
+ * the two other axes:
  *   A   = (psi1[c] - psi1[c-e]) / (psi1[c] + psi1[c-e] + eps)
  *   B_a = 1/2 (S(c+e_a) - S(c-e_a)) / (S(c+e_a) + S(c-e_a) + eps),
  *         S(x) = psi1[x] + psi1[x-e]            (the pair across the face)
@@ -180,20 +201,94 @@ static double antidiffusive_velocity(const oracle_cfg *c, const double *h, const
 }
 
 /* (a3): maximum (sign=+1) or minimum (sign=-1) over the cell and its six
- * face neighbours of both psi^n and psi1 (Listing 1, stage 8). */
-static double local_extremum(const oracle_cfg *c, const double *psi, const double *psi1,
+ * face neighbours (Listing 1, stage 8) of the corrected field p and, unless
+ * c->extrema is 1, of psi^n. */
+static double local_extremum(const oracle_cfg *c, const double *psi, const double *p,
                              int i, int j, int k, int sign)
 {
     static const int off[7][3] = {{0, 0, 0}, {-1, 0, 0}, {1, 0, 0}, {0, -1, 0},
                                   {0, 1, 0}, {0, 0, -1}, {0, 0, 1}};
-    double m = at(c, psi, i, j, k);
+    double m = at(c, p, i, j, k);
     for (int n = 0; n < 7; ++n) {
-        double a = at(c, psi, i + off[n][0], j + off[n][1], k + off[n][2]);
-        double b = at(c, psi1, i + off[n][0], j + off[n][1], k + off[n][2]);
-        if (sign > 0) m = fmax(m, fmax(a, b));
-        else m = fmin(m, fmin(a, b));
+        double b = at(c, p, i + off[n][0], j + off[n][1], k + off[n][2]);
+        m = sign > 0 ? fmax(m, b) : fmin(m, b);
+        if (c->extrema == 0) {
+            double a = at(c, psi, i + off[n][0], j + off[n][1], k + off[n][2]);
+            m = sign > 0 ? fmax(m, a) : fmin(m, a);
+        }
     }
     return m;
+}
+
+/* One corrective pass (a2)-(a6): the field p (the result of the pass before)
+ * is corrected with pseudo-velocities built from p and the face velocities
+ * w that the pass before used.  v receives the pseudo-velocities, vm the
+ * velocities this pass transports with (v limited, or v itself), next the
+ * corrected field.  bup/bdn are work arrays. */
+static void corrective_pass(const oracle_cfg *c, const double *h, const double *psi,
+                            const double *p, const double *w[3], double *v[3], double *vm[3],
+                            double *bup, double *bdn, double *next)
+{
+    long n = (long)c->nx * c->ny * c->nz;
+
+    /* (a2) antidiffusive pseudo-velocities on every lower face */
+    for (int d = 0; d < 3; ++d) {
+        double *vd = v[d];
+#pragma omp parallel for collapse(2) schedule(static)
+        for (int k = 0; k < c->nz; ++k)
+            for (int j = 0; j < c->ny; ++j)
+                for (int i = 0; i < c->nx; ++i)
+                    vd[lin(c, i, j, k)] = antidiffusive_velocity(c, h, p, w, d, i, j, k);
+    }
+
+    if (c->nonoscillatory) {
+        /* (a3) + (a4): extrema and limiter factors per cell */
+#pragma omp parallel for collapse(2) schedule(static)
+        for (int k = 0; k < c->nz; ++k)
+            for (int j = 0; j < c->ny; ++j)
+                for (int i = 0; i < c->nx; ++i) {
+                    double mx = local_extremum(c, psi, p, i, j, k, +1);
+                    double mn = local_extremum(c, psi, p, i, j, k, -1);
+                    double pc = at(c, p, i, j, k);
+                    double in = 0.0, outf = 0.0;
+                    for (int d = 0; d < 3; ++d) {
+                        int e[3] = {0, 0, 0};
+                        e[d] = 1;
+                        double vlo = face(c, v[d], d, i, j, k);
+                        double vhi = face(c, v[d], d, i + e[0], j + e[1], k + e[2]);
+                        in += fmax(vlo, 0.0) * at(c, p, i - e[0], j - e[1], k - e[2]) -
+                              fmin(vhi, 0.0) * at(c, p, i + e[0], j + e[1], k + e[2]);
+                        outf += fmax(vhi, 0.0) * pc - fmin(vlo, 0.0) * pc;
+                    }
+                    double hc = at(c, h, i, j, k);
+                    bup[lin(c, i, j, k)] = (mx - pc) * hc / (in + c->eps);
+                    bdn[lin(c, i, j, k)] = (pc - mn) * hc / (outf + c->eps);
+                }
+        /* (a5): limited velocities on every lower face, between L = c-e and R = c */
+        for (int d = 0; d < 3; ++d) {
+            double *vd = v[d], *vmd = vm[d];
+#pragma omp parallel for collapse(2) schedule(static)
+            for (int k = 0; k < c->nz; ++k)
+                for (int j = 0; j < c->ny; ++j)
+                    for (int i = 0; i < c->nx; ++i) {
+                        int idx[3] = {i, j, k};
+                        long cR = lin(c, i, j, k);
+                        if (!c->periodic[d] && idx[d] == 0) { vmd[cR] = 0.0; continue; }
+                        int e[3] = {0, 0, 0};
+                        e[d] = 1;
+                        double bupL = at(c, bup, i - e[0], j - e[1], k - e[2]);
+                        double bdnL = at(c, bdn, i - e[0], j - e[1], k - e[2]);
+                        double V = vd[cR];
+                        vmd[cR] = fmax(V, 0.0) * fmin(1.0, fmin(bdnL, bup[cR])) +
+                                  fmin(V, 0.0) * fmin(1.0, fmin(bupL, bdn[cR]));
+                    }
+        }
+    } else {
+        for (int d = 0; d < 3; ++d) memcpy(vm[d], v[d], sizeof(double) * n);
+    }
+
+    /* (a6) corrective donor-cell pass of p with the (limited) velocities */
+    donor_pass(c, h, p, vm[0], vm[1], vm[2], next);
 }
 
 static int run_step(const oracle_cfg *c, const double *h, const double *psi,
@@ -201,9 +296,23 @@ static int run_step(const oracle_cfg *c, const double *h, const double *psi,
                     double *out, oracle_stages *st)
 {
     long n = (long)c->nx * c->ny * c->nz;
-    const double *u[3] = {u1, u2, u3};
-    double *psi1 = malloc(sizeof(double) * n);
-    if (!psi1) return -1;
+    /* work arrays: psi1, the field after pass 2, V[3], Vmon[3], the
+     * velocities of the pass before [3], beta_up, beta_dn */
+    enum { NWORK = 13 };
+    double *wk[NWORK];
+    int nwork = c->iterations <= 1 ? 1 : NWORK;
+    for (int a = 0; a < NWORK; ++a) wk[a] = NULL;
+    for (int a = 0; a < nwork; ++a) {
+        wk[a] = malloc(sizeof(double) * n);
+        if (!wk[a]) {
+            for (int b = 0; b < a; ++b) free(wk[b]);
+            return -1;
+        }
+    }
+    double *psi1 = wk[0], *psi2 = wk[1];
+    double *v[3] = {wk[2], wk[3], wk[4]}, *vm[3] = {wk[5], wk[6], wk[7]};
+    double *wprev[3] = {wk[8], wk[9], wk[10]};
+    double *bup = wk[11], *bdn = wk[12];
 
     /* (a1) donor-cell pass */
     donor_pass(c, h, psi, u1, u2, u3, psi1);
@@ -214,71 +323,10 @@ static int run_step(const oracle_cfg *c, const double *h, const double *psi,
         return 0;
     }
 
-    double *v[3], *bup = NULL, *bdn = NULL, *vm[3] = {NULL, NULL, NULL};
-    for (int d = 0; d < 3; ++d) v[d] = malloc(sizeof(double) * n);
-    bup = malloc(sizeof(double) * n);
-    bdn = malloc(sizeof(double) * n);
-    for (int d = 0; d < 3; ++d) vm[d] = malloc(sizeof(double) * n);
-    int ok = bup && bdn;
-    for (int d = 0; d < 3; ++d) ok = ok && v[d] && vm[d];
-    if (!ok) {
-        for (int d = 0; d < 3; ++d) { free(v[d]); free(vm[d]); }
-        free(bup); free(bdn); free(psi1);
-        return -1;
-    }
-
-    /* (a2) antidiffusive pseudo-velocities on every lower face */
-    for (int d = 0; d < 3; ++d)
-        for (int k = 0; k < c->nz; ++k)
-            for (int j = 0; j < c->ny; ++j)
-                for (int i = 0; i < c->nx; ++i)
-                    v[d][lin(c, i, j, k)] = antidiffusive_velocity(c, h, psi1, u, d, i, j, k);
-
-    if (c->nonoscillatory) {
-        /* (a3) + (a4): extrema and limiter factors per cell */
-        for (int k = 0; k < c->nz; ++k)
-            for (int j = 0; j < c->ny; ++j)
-                for (int i = 0; i < c->nx; ++i) {
-                    double mx = local_extremum(c, psi, psi1, i, j, k, +1);
-                    double mn = local_extremum(c, psi, psi1, i, j, k, -1);
-                    double p1 = at(c, psi1, i, j, k);
-                    double in = 0.0, outf = 0.0;
-                    for (int d = 0; d < 3; ++d) {
-                        int e[3] = {0, 0, 0};
-                        e[d] = 1;
-                        double vlo = face(c, v[d], d, i, j, k);
-                        double vhi = face(c, v[d], d, i + e[0], j + e[1], k + e[2]);
-                        in += fmax(vlo, 0.0) * at(c, psi1, i - e[0], j - e[1], k - e[2]) -
-                              fmin(vhi, 0.0) * at(c, psi1, i + e[0], j + e[1], k + e[2]);
-                        outf += fmax(vhi, 0.0) * p1 - fmin(vlo, 0.0) * p1;
-                    }
-                    double hc = at(c, h, i, j, k);
-                    bup[lin(c, i, j, k)] = (mx - p1) * hc / (in + c->eps);
-                    bdn[lin(c, i, j, k)] = (p1 - mn) * hc / (outf + c->eps);
-                }
-        /* (a5): limited velocities on every lower face, between L = c-e and R = c */
-        for (int d = 0; d < 3; ++d)
-            for (int k = 0; k < c->nz; ++k)
-                for (int j = 0; j < c->ny; ++j)
-                    for (int i = 0; i < c->nx; ++i) {
-                        int idx[3] = {i, j, k};
-                        long cR = lin(c, i, j, k);
-                        if (!c->periodic[d] && idx[d] == 0) { vm[d][cR] = 0.0; continue; }
-                        int e[3] = {0, 0, 0};
-                        e[d] = 1;
-                        double bupL = at(c, bup, i - e[0], j - e[1], k - e[2]);
-                        double bdnL = at(c, bdn, i - e[0], j - e[1], k - e[2]);
-                        double V = v[d][cR];
-                        vm[d][cR] = fmax(V, 0.0) * fmin(1.0, fmin(bdnL, bup[cR])) +
-                                    fmin(V, 0.0) * fmin(1.0, fmin(bupL, bdn[cR]));
-                    }
-    } else {
-        for (int d = 0; d < 3; ++d) memcpy(vm[d], v[d], sizeof(double) * n);
-    }
-
-    /* (a6) corrective donor-cell pass of psi1 with the (limited) velocities */
-    donor_pass(c, h, psi1, vm[0], vm[1], vm[2], out);
-
+    /* first corrective pass: psi1 corrected, pseudo-velocities from U */
+    const double *w[3] = {u1, u2, u3};
+    double *next = c->iterations == 2 ? out : psi2;
+    corrective_pass(c, h, psi, psi1, w, v, vm, bup, bdn, next);
     if (st) {
         double **dst_v[3] = {&st->v1, &st->v2, &st->v3};
         double **dst_m[3] = {&st->vm1, &st->vm2, &st->vm3};
@@ -295,15 +343,24 @@ static int run_step(const oracle_cfg *c, const double *h, const double *psi,
             else memset(st->beta_dn, 0, sizeof(double) * n);
         }
     }
-    for (int d = 0; d < 3; ++d) { free(v[d]); free(vm[d]); }
-    free(bup); free(bdn); free(psi1);
+
+    if (c->iterations == 3) {
+        /* second corrective pass: psi2 corrected, pseudo-velocities built
+         * from the velocities the first corrective pass transported with */
+        for (int d = 0; d < 3; ++d) memcpy(wprev[d], vm[d], sizeof(double) * n);
+        const double *w2[3] = {wprev[0], wprev[1], wprev[2]};
+        corrective_pass(c, h, psi, psi2, w2, v, vm, bup, bdn, out);
+    }
+
+    for (int a = 0; a < nwork; ++a) free(wk[a]);
     return 0;
 }
 
 static int cfg_ok(const oracle_cfg *c)
 {
     if (!c || c->nx <= 0 || c->ny <= 0 || c->nz <= 0) return 0;
-    if (c->iterations != 1 && c->iterations != 2) return 0;
+    if (c->iterations < 1 || c->iterations > 3) return 0;
+    if (c->extrema != 0 && c->extrema != 1) return 0;
     if (!(c->eps > 0.0)) return 0;
     return 1;
 }
@@ -346,4 +403,14 @@ double oracle_mass(long n, const double *h, const double *psi)
         s = t;
     }
     return s + comp;
+}
+
+/* Number of threads the per-cell loops use (1 in the serial build). */
+int oracle_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
 }

@@ -13,20 +13,26 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "mpdata_oracle.c")
 _BUILD = os.path.join(_HERE, "_build", platform.machine())
 _LIB = None
+_LIB_OMP = None
 
 
-def lib_path() -> str:
-    return os.path.join(_BUILD, "libmpdata_oracle.so")
+def lib_path(omp: bool = False) -> str:
+    return os.path.join(_BUILD, "libmpdata_oracle_omp.so" if omp else "libmpdata_oracle.so")
 
 
-def build(force: bool = False, src: str = _SRC, out: str | None = None) -> str:
-    """Compile the oracle (or a copy of its source) into a shared library."""
-    out = out or lib_path()
+def build(force: bool = False, src: str = _SRC, out: str | None = None, omp: bool = False) -> str:
+    """Compile the oracle (or a copy of its source) into a shared library.
+
+    omp=True builds the same source with -fopenmp: the per-cell loops run on
+    all host cores and return the serial build's bits."""
+    out = out or lib_path(omp)
     os.makedirs(os.path.dirname(out), exist_ok=True)
     if force or not os.path.exists(out) or os.path.getmtime(out) < os.path.getmtime(src):
         tmp = out + ".tmp%d" % os.getpid()
-        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-std=c99", "-fPIC",
-                               "-shared", src, "-o", tmp, "-lm"])
+        cmd = ["gcc", "-O2", "-ffp-contract=off", "-std=c99", "-fPIC", "-shared"]
+        if omp:
+            cmd.append("-fopenmp")
+        subprocess.check_call(cmd + [src, "-o", tmp, "-lm"])
         os.replace(tmp, out)
     return out
 
@@ -34,7 +40,8 @@ def build(force: bool = False, src: str = _SRC, out: str | None = None) -> str:
 class _Cfg(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
                 ("periodic", ctypes.c_int * 3), ("iterations", ctypes.c_int),
-                ("nonoscillatory", ctypes.c_int), ("eps", ctypes.c_double)]
+                ("nonoscillatory", ctypes.c_int), ("eps", ctypes.c_double),
+                ("extrema", ctypes.c_int)]
 
 
 class _Stages(ctypes.Structure):
@@ -51,18 +58,22 @@ class Config:
     iterations: int = 2
     nonoscillatory: int = 1
     eps: float = 1e-15
+    extrema: int = 0  # 0: psi^n and the corrected field; 1: the corrected field only
 
     def c(self) -> _Cfg:
         return _Cfg(self.nx, self.ny, self.nz, (ctypes.c_int * 3)(*self.periodic),
-                    self.iterations, self.nonoscillatory, self.eps)
+                    self.iterations, self.nonoscillatory, self.eps, self.extrema)
 
 
-def load(path: str | None = None):
-    """Load the oracle library (building it first if needed)."""
-    global _LIB
-    if path is None and _LIB is not None:
+def load(path: str | None = None, omp: bool = False):
+    """Load the oracle library (building it first if needed); omp=True loads
+    the OpenMP build."""
+    global _LIB, _LIB_OMP
+    if path is None and omp and _LIB_OMP is not None:
+        return _LIB_OMP
+    if path is None and not omp and _LIB is not None:
         return _LIB
-    lib = ctypes.CDLL(path or build())
+    lib = ctypes.CDLL(path or build(omp=omp))
     P = ctypes.c_void_p
     lib.oracle_step.argtypes = [ctypes.POINTER(_Cfg), P, P, P, P, P, P, ctypes.POINTER(_Stages)]
     lib.oracle_step.restype = ctypes.c_int
@@ -70,9 +81,18 @@ def load(path: str | None = None):
     lib.oracle_run.restype = ctypes.c_int
     lib.oracle_mass.argtypes = [ctypes.c_long, P, P]
     lib.oracle_mass.restype = ctypes.c_double
-    if path is None:
+    lib.oracle_threads.argtypes = []
+    lib.oracle_threads.restype = ctypes.c_int
+    if path is None and omp:
+        _LIB_OMP = lib
+    elif path is None:
         _LIB = lib
     return lib
+
+
+def threads(lib=None) -> int:
+    """Threads the library's per-cell loops use (1 for the serial build)."""
+    return int((lib or load()).oracle_threads())
 
 
 def _arr(a, shape) -> np.ndarray:

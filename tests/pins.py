@@ -29,6 +29,17 @@ axis, h in the wrong place, a limiter that does nothing.
   lid_wall         a lid is a reflecting wall: a lid domain of n cells gives
                    the first half of the periodic domain of 2n cells that
                    holds the mirror-extended problem.
+  local_bounds     the limiter's defining property: each corrected value lies
+                   within the extrema of its 7-point stencil over the chosen
+                   set (psi^n and the corrected field, or the corrected field
+                   alone), for any h > 0 and any flow, with 2 or 3 passes.
+  extrema_set      the two sets differ where they should: with psi^n in the
+                   set a corrective pass may rebuild a peak that the donor
+                   pass flattened; without it, it may not.
+  iterations3      a second corrective pass lowers the error of a smooth
+                   solution and keeps the second order.
+
+Shift, constant and mass also run with three passes.
 """
 from __future__ import annotations
 
@@ -43,9 +54,10 @@ def _rng(seed):
     return np.random.default_rng(seed)
 
 
-def _run(lib, shape, h, psi, u, nsteps, periodic=(1, 1, 1), iterations=2, nonosc=1, eps=1e-15):
+def _run(lib, shape, h, psi, u, nsteps, periodic=(1, 1, 1), iterations=2, nonosc=1, eps=1e-15,
+         extrema=0):
     nz, ny, nx = shape
-    cfg = O.Config(nx, ny, nz, tuple(periodic), iterations, nonosc, eps)
+    cfg = O.Config(nx, ny, nz, tuple(periodic), iterations, nonosc, eps, extrema)
     return O.run(cfg, h, psi, u[0], u[1], u[2], nsteps, lib=lib)
 
 
@@ -62,12 +74,12 @@ def pin_shift(lib, steps=3):
     h = np.ones(shape)
     for axis in range(3):
         for sign in (1.0, -1.0):
-            for nonosc in (0, 1):
+            for nonosc, iterations in ((0, 2), (1, 2), (1, 3)):
                 u = [np.zeros(shape) for _ in range(3)]
                 u[axis][:] = sign
-                out = _run(lib, shape, h, psi, u, steps, nonosc=nonosc)
+                out = _run(lib, shape, h, psi, u, steps, nonosc=nonosc, iterations=iterations)
                 want = np.roll(psi, int(sign) * steps, axis=2 - axis)
-                assert np.array_equal(out, want), ("shift", axis, sign, nonosc)
+                assert np.array_equal(out, want), ("shift", axis, sign, nonosc, iterations)
 
 
 def pin_constant(lib, steps=3):
@@ -78,8 +90,9 @@ def pin_constant(lib, steps=3):
     psi = np.full(shape, c)
     h = r.uniform(0.5, 2.0, size=shape)
     u = [np.full(shape, v) for v in (0.3, -0.2, 0.1)]
-    out = _run(lib, shape, h, psi, u, steps)
-    assert np.array_equal(out, psi), "constant: constant U, random h"
+    for iterations, extrema in ((2, 0), (3, 0), (3, 1)):
+        out = _run(lib, shape, h, psi, u, steps, iterations=iterations, extrema=extrema)
+        assert np.array_equal(out, psi), ("constant: constant U, random h", iterations, extrema)
     nz, ny, nx = 6, 10, 12
     u1, u2, u3 = F.rotation_courant(nx, ny, nz, 0.5)
     h = F.sine_density(nx, ny, nz)
@@ -111,10 +124,11 @@ def pin_mass(lib, steps=5):
                 sl[2 - d] = 0
                 u[d][tuple(sl)] = 0.0
         m0 = O.mass(h, psi, lib=lib)
-        for nonosc in (0, 1):
-            out = _run(lib, shape, h, psi, u, steps, periodic=periodic, nonosc=nonosc)
+        for nonosc, iterations in ((0, 2), (1, 2), (1, 3)):
+            out = _run(lib, shape, h, psi, u, steps, periodic=periodic, nonosc=nonosc,
+                       iterations=iterations)
             m1 = O.mass(h, out, lib=lib)
-            assert abs(m1 / m0 - 1.0) <= 1e-12, ("mass", periodic, nonosc, m1 / m0 - 1.0)
+            assert abs(m1 / m0 - 1.0) <= 1e-12, ("mass", periodic, nonosc, iterations, m1 / m0 - 1.0)
 
 
 def pin_positivity(lib, steps=10):
@@ -309,5 +323,103 @@ def pin_lid_wall(lib, steps=3):
             assert np.allclose(a, b, rtol=1e-13, atol=0), ("lid_wall", lid, nonosc)
 
 
+def _stencil(f, periodic):
+    """f and its six face neighbours (c - e_d, c + e_d for each axis d):
+    wrapped on a periodic axis, an edge copy beyond a lid."""
+    out = [f]
+    for d in range(3):
+        a = 2 - d
+        pad = [(0, 0)] * 3
+        pad[a] = (1, 1)
+        g = np.pad(f, pad, mode="wrap" if periodic[d] else "edge")
+        n = f.shape[a]
+        out.append(np.take(g, np.arange(0, n), axis=a))
+        out.append(np.take(g, np.arange(2, n + 2), axis=a))
+    return out
+
+
+def _bounds(fields, periodic):
+    vals = [v for f in fields for v in _stencil(f, periodic)]
+    return np.maximum.reduce(vals), np.minimum.reduce(vals)
+
+
+def _spiky_problem(seed, shape, umax, lid):
+    h, _, u = _random_problem(seed, shape, umax=umax, lid=lid)
+    r = _rng(seed + 100)
+    psi = 0.01 + 10.0 * r.uniform(0.0, 1.0, size=shape) ** 6  # rough, strictly positive
+    return h, psi, u
+
+
+def pin_local_bounds(lib):
+    """Corrected value within the stencil extrema of the bounding set.  From
+    the limiter's definition: the limited inflow of a cell is at most
+    beta_up * IN, so the pass adds at most (psi_max - p) h IN / (IN + eps) / h
+    to p; likewise for the outflow and psi_min (requires psi >= 0)."""
+    shape = (6, 7, 8)
+    for seed, periodic, lid in ((20, (1, 1, 1), None), (21, (1, 1, 0), 2), (22, (0, 1, 1), 0)):
+        h, psi, u = _spiky_problem(seed, shape, 0.15, lid)
+        tol = 1e-12 * psi.max()
+        for iterations in (2, 3):
+            for extrema in (0, 1):
+                if iterations == 2:
+                    nz, ny, nx = shape
+                    cfg = O.Config(nx, ny, nz, periodic, 1, 1, 1e-15)
+                    prev = O.step(cfg, h, psi, u[0], u[1], u[2], lib=lib)
+                else:
+                    prev = _run(lib, shape, h, psi, u, 1, periodic=periodic, iterations=2,
+                                extrema=extrema)
+                mx, mn = _bounds([psi, prev] if extrema == 0 else [prev], periodic)
+                out = _run(lib, shape, h, psi, u, 1, periodic=periodic, iterations=iterations,
+                           extrema=extrema)
+                assert np.all(out <= mx + tol) and np.all(out >= mn - tol), \
+                    ("local_bounds", periodic, iterations, extrema,
+                     float((out - mx).max()), float((mn - out).max()))
+
+
+def pin_extrema_set(lib):
+    """A one-cell spike moving at C = 0.3: the donor pass lowers it to 0.7 of
+    its height; with psi^n in the bounding set the corrective pass raises it
+    above that again, with the corrected field alone it stays at or below."""
+    n = 24
+    shp = _axis_shape(0, n)
+    psi = np.full(shp, 0.1)
+    psi.reshape(-1)[10] = 1.0
+    u = [np.zeros(shp) for _ in range(3)]
+    u[0][:] = 0.3
+    h = np.ones(shp)
+    cfg = O.Config(n, 1, 1, (1, 1, 1), 1, 1, 1e-15)
+    psi1 = O.step(cfg, h, psi, u[0], u[1], u[2], lib=lib)
+    mx1, _ = _bounds([psi1], (1, 1, 1))
+    both = _run(lib, shp, h, psi, u, 1, extrema=0)
+    only = _run(lib, shp, h, psi, u, 1, extrema=1)
+    assert np.all(only <= mx1 + 1e-14), ("extrema_set: corrected-field-only bound", float((only - mx1).max()))
+    assert (both - mx1).max() > 1e-3, ("extrema_set: psi^n not in the default set", float((both - mx1).max()))
+
+
+def _err_1d(lib, axis, n, C, hvar, nonosc, iterations):
+    shp = _axis_shape(axis, n)
+    psi = _gauss_1d(n, n / 16).reshape(shp)
+    x = np.arange(n) + 0.5
+    h = (1.0 + hvar * np.sin(2 * np.pi * x / n)).reshape(shp)
+    u = [np.zeros(shp) for _ in range(3)]
+    u[axis][:] = C
+    out = _run(lib, shp, h, psi, u, int(round(n / abs(C))), nonosc=nonosc, iterations=iterations)
+    return math.sqrt(np.mean((out - psi) ** 2))
+
+
+def pin_iterations3(lib, sizes=(64, 128, 256)):
+    """Each corrective pass estimates and removes the leading error of the
+    pass before (Smolarkiewicz 1984): a second one must lower the error of a
+    smooth transit and keep second-order convergence."""
+    for axis, C, hvar in ((0, 0.25, 0.0), (2, -0.5, 0.2), (1, 0.5, 0.0)):
+        for nonosc in (0, 1):
+            e2 = _err_1d(lib, axis, sizes[1], C, hvar, nonosc, 2)
+            e3 = [_err_1d(lib, axis, n, C, hvar, nonosc, 3) for n in sizes]
+            assert e3[1] <= 0.9 * e2, ("iterations3: no gain", axis, C, hvar, nonosc, e3[1] / e2)
+            orders = [math.log2(e3[i] / e3[i + 1]) for i in range(len(e3) - 1)]
+            assert min(orders) >= 1.75, ("iterations3: order", axis, C, hvar, nonosc, orders)
+
+
 FAST_PINS = [pin_shift, pin_constant, pin_lid_face, pin_lid_wall, pin_mass, pin_scale, pin_mirror,
-             pin_permute, pin_positivity, pin_monotone, pin_binomial]
+             pin_permute, pin_positivity, pin_monotone, pin_binomial, pin_local_bounds,
+             pin_extrema_set, pin_iterations3]
