@@ -11,12 +11,19 @@ Prints ONE JSON line (rank 0):
              memory (copies of the 5 inputs in and psi out inside the region)
   roofline   the fused kernel against the measured HBM copy peak under the
              6-field model (24 B per cell-step in FP32)
-  cpu_baseline  the FP64 oracle on a bounded sample of the same workload
+  cpu_baseline  the FP64 oracle (its OpenMP build, all host cores) on a
+             bounded sample of the same workload
   clocks     nvidia-smi samples taken during the timed region
+  ci95_pct   95 % Student-t half-width of the per-solve times, % of the mean
 
---impl reference times the FP64 oracle (the serial CPU reference) on a
-bounded sample per step.  Under torchrun (N > 1) every rank runs its own
-replica of the problem (the workload does not shard across GPUs here).
+--impl reference times the FP64 oracle (the CPU reference) on a bounded
+sample per step.  Under torchrun (N > 1) every rank runs its own replica of
+the problem (the workload does not shard across GPUs here).
+
+Other workloads (--workload): tracers (64 uneven grids in one batched
+launch), serve (Poisson arrivals through the serving runtime) and precision
+(FP32 / FP32 with FP64 limiter sums / FP64, three passes and the
+corrected-field extrema set on a 2048x1024x64 grid with a 1e-6 background).
 """
 from __future__ import annotations
 
@@ -51,9 +58,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
-    ap.add_argument("--workload", default="grid", choices=["grid", "tracers", "serve"],
+    ap.add_argument("--workload", default="grid", choices=["grid", "tracers", "serve", "precision"],
                     help="grid: 1024x512x64 (default); tracers: 64 uneven grids batched; "
-                         "serve: Poisson arrivals through the serving runtime vs one solve per launch")
+                         "serve: Poisson arrivals through the serving runtime vs one solve per launch; "
+                         "precision: FP32/FP64 modes on 2048x1024x64 against the oracle")
     ap.add_argument("--serve-seconds", type=float, default=10.0)
     ap.add_argument("--serve-rate", type=float, default=200.0)
     return ap.parse_args()
@@ -91,15 +99,25 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
+FUSED_SOURCES = ("mpdata_fused2.cu", "mpdata_fused.cu", "mpdata_internal.cuh")
+
+
+def fused_source_sha256():
+    h = hashlib.sha256()
+    for name in FUSED_SOURCES:
+        with open(os.path.join(ROOT, "paper_1507_01265_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
 def kernel_traffic(ncells):
     """DRAM bytes per launch of the fused kernel from the committed ncu
-    summary, valid only while the kernel source is unchanged."""
+    summary, valid only while the kernel sources are unchanged."""
     path = os.path.join(ROOT, "profiles", "fused_traffic.json")
     try:
         with open(path) as f:
             rec = json.load(f)
-        src = open(os.path.join(ROOT, "paper_1507_01265_gb300", "csrc", "mpdata_fused.cu"), "rb").read()
-        if rec.get("source_sha256") != hashlib.sha256(src).hexdigest():
+        if rec.get("source_sha256") != fused_source_sha256():
             return None
         return float(rec["bytes_per_cell"]) * ncells
     except Exception:
@@ -169,47 +187,72 @@ def oracle_setup(rows):
     return oracle.Config(f.nx, rows, f.nz, (1, 1, 0)), arrs
 
 
-def oracle_time(cfg, arrs):
-    """Seconds for one oracle step on the slab (serial FP64 C, one core)."""
+def oracle_lib(all_cores=True):
+    """(library, threads, description): the oracle's OpenMP build when it
+    loads (every host core), else the serial build."""
+    import oracle
+    if all_cores:
+        try:
+            lib = oracle.load(omp=True)
+            n = oracle.threads(lib)
+            return lib, n, "FP64 C oracle, OpenMP build, %d threads" % n
+        except Exception:
+            pass
+    return oracle.load(), 1, "FP64 C oracle, serial build"
+
+
+def oracle_time(cfg, arrs, lib=None):
+    """Seconds for one oracle step on the slab."""
     import oracle
     t0 = time.perf_counter()
-    oracle.run(cfg, *arrs, nsteps=1)
+    oracle.run(cfg, *arrs, nsteps=1, lib=lib)
     return time.perf_counter() - t0
 
 
-def oracle_sample(rows=64):
+def oracle_sample(rows=512, serial_rows=32):
     """Time the FP64 oracle, as it stands, on a bounded sample of the
-    workload: one step of the first `rows` y-rows of the 1024x512x64 grid."""
+    workload: one step of the first `rows` y-rows of the 1024x512x64 grid on
+    all host cores (OpenMP build), and one step of `serial_rows` rows on one
+    core (serial build)."""
+    import oracle
+    lib, threads, what = oracle_lib()
     cfg, arrs = oracle_setup(rows)
-    dt = oracle_time(cfg, arrs)
+    dt = oracle_time(cfg, arrs, lib)
     cells = cfg.nx * cfg.ny * cfg.nz
-    return {"value": cells / dt / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+    scfg, sarrs = oracle_setup(serial_rows)
+    sdt = oracle_time(scfg, sarrs, oracle.load())
+    return {"value": cells / dt / 1e9, "unit": UNIT, "cores": threads, "kind": "oracle",
             "sample": "1 step of a %dx%dx%d slab (first %d y-rows) of the 1024x512x64 workload, "
-                      "serial FP64 C, %.1f s" % (cfg.nx, rows, cfg.nz, rows, dt)}
+                      "%s, %.1f s wall" % (cfg.nx, rows, cfg.nz, rows, what, dt),
+            "serial": {"value": scfg.nx * serial_rows * scfg.nz / sdt / 1e9, "cores": 1,
+                       "sample": "1 step of a %dx%dx%d slab, serial build, %.1f s"
+                                 % (scfg.nx, serial_rows, scfg.nz, sdt)}}
 
 
 def run_reference(args, rank, world):
     """The oracle as the reference arm: each bench step is one oracle step on
-    a 1024x16x64 slab of the same workload."""
+    a 1024x64x64 slab of the same workload, on all host cores."""
     if rank != 0:
         return 0
-    rows = 16
+    rows = 64
+    lib, threads, what = oracle_lib()
     cfg, arrs = oracle_setup(rows)
     cells = cfg.nx * cfg.ny * cfg.nz
     for _ in range(args.warmup):
-        oracle_time(cfg, arrs)
-    times = [oracle_time(cfg, arrs) for _ in range(args.steps)]
+        oracle_time(cfg, arrs, lib)
+    times = [oracle_time(cfg, arrs, lib) for _ in range(args.steps)]
     t = sum(times)
     v = cells * len(times) / t / 1e9
     sample = ("each step: 1 step of a %dx%dx%d slab (first %d y-rows) of the 1024x512x64 "
-              "workload, serial FP64 C" % (cfg.nx, rows, cfg.nz, rows))
+              "workload, %s" % (cfg.nx, rows, cfg.nz, rows, what))
     line = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * t / len(times), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "impl": "reference",
             "config": {"workload": "rotation_blobs 1024x512x64, periodic x/y, lid z (sampled slab)",
                        "grid": [NX, NY, NZ], "sample_grid": [cfg.nx, rows, cfg.nz]},
-            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": sample},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -374,6 +417,123 @@ def run_serve(args):
     return 0
 
 
+PRECISION_MODES = [  # name, dtype, path, iterations, extrema, precision
+    ("f32", "f32", "fused", 2, "both", "pure"),
+    ("f32_stages", "f32", "stages", 2, "both", "pure"),
+    ("f32_f64beta", "f32", "stages", 2, "both", "f64_beta"),
+    ("f64", "f64", "fused", 2, "both", "pure"),
+    ("f32_iter3", "f32", "stages", 3, "both", "pure"),
+    ("f64_iter3", "f64", "stages", 3, "both", "pure"),
+    ("f32_extrema_corrected", "f32", "stages", 2, "corrected", "pure"),
+    ("f64_extrema_corrected", "f64", "stages", 2, "corrected", "pure"),
+]
+
+
+def _errors(got, want, background):
+    """Error summary of got against want (float64 arrays of one shape)."""
+    import numpy as np
+    d = np.abs(got - want)
+    rel = d / np.maximum(np.abs(want), 1e-300)
+    bg = want < background
+    return {"max_abs_over_max": float(d.max() / np.abs(want).max()),
+            "l2_rel": float(np.sqrt((d ** 2).sum() / (want ** 2).sum())),
+            "max_pointwise_rel": float(rel.max()),
+            "max_pointwise_rel_background": float(rel[bg].max()) if bg.any() else None,
+            "background_cells": int(bg.sum())}
+
+
+def run_precision(args):
+    """Precision study: the 2048x1024x64 rotation grid with blobs on a 1e-6
+    background, 100 steps, in every arithmetic mode and scheme variant.
+    Error against the FP64 oracle on a 256x128x64 copy (psi and h every 8th
+    cell in x and y, rotation regenerated at that size); error against the
+    FP64 GPU mode, mass drift and time on the full grid."""
+    import numpy as np
+    import torch
+    import gen.fields as F
+    import oracle
+    import paper_1507_01265_gb300 as mp
+    nsteps = 100
+    dev = torch.device("cuda")
+    full = F.precision_grid(nsteps=nsteps)
+    small = F.subsample(full, 8)
+    background = 1e-5  # cells below this are background (1e-6) in the result
+
+    def solve(f, mode, psi_dev=None):
+        _, dtype, path, it, ext, prec = mode
+        td = torch.float64 if dtype == "f64" else torch.float32
+        t = [torch.from_numpy(a).to(dev, td) for a in (f.h, f.psi, f.u1, f.u2, f.u3)]
+        with mp.Solver(f.nx, f.ny, f.nz, periodic=f.periodic, dtype=dtype, path=path,
+                       iterations=it, extrema=ext, precision=prec) as s:
+            m0 = s.mass(t[0], t[1]).cpu().numpy()
+            if f is full:  # warm-up solve (then restore psi), timed solve
+                p0 = t[1].clone()
+                s.step(*t, 2)
+                t[1].copy_(p0)
+                del p0
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            s.step(*t, nsteps)
+            e1.record()
+            torch.cuda.synchronize()
+            m1 = s.mass(t[0], t[1]).cpu().numpy()
+        ms = e0.elapsed_time(e1)
+        out = t[1]
+        del t
+        return out, {"gcell_steps_per_s": f.ncells * nsteps / (ms * 1e-3) / 1e9,
+                     "mass_drift": float(m1[0] / m0[0] - 1.0), "min": float(m1[1]),
+                     "max": float(m1[2])}
+
+    # oracle on the small copy, one run per scheme variant
+    lib, threads, what = oracle_lib()
+    ref = {}
+    t_oracle = 0.0
+    for it, ext in ((2, "both"), (3, "both"), (2, "corrected")):
+        cfg = oracle.Config(small.nx, small.ny, small.nz, small.periodic, it, 1, 1e-15,
+                            0 if ext == "both" else 1)
+        t0 = time.perf_counter()
+        ref[(it, ext)] = oracle.run(cfg, *small.as_f64(), nsteps=nsteps, lib=lib)
+        t_oracle += time.perf_counter() - t0
+    m_small0 = oracle.mass(*small.as_f64()[:2])
+    oracle_mass = {"%d_%s" % k: float(oracle.mass(small.as_f64()[0], v) / m_small0 - 1.0)
+                   for k, v in ref.items()}
+
+    modes = {}
+    f64_full = None
+    for mode in PRECISION_MODES:
+        name, dtype, path, it, ext, prec = mode
+        got, _ = solve(small, mode)
+        rec = {"dtype": dtype, "path": path, "iterations": it, "extrema": ext, "precision": prec,
+               "vs_oracle_256x128x64": _errors(got.double().cpu().numpy(), ref[(it, ext)], background)}
+        out, stats = solve(full, mode)
+        rec["full_2048x1024x64"] = stats
+        if name == "f64":
+            f64_full = out.cpu().numpy()
+        modes[name] = rec
+        del out
+        torch.cuda.empty_cache()
+    # mode vs mode on the full grid, against the FP64 GPU result (same scheme)
+    for name in ("f32", "f32_stages", "f32_f64beta"):
+        out, _ = solve(full, next(m for m in PRECISION_MODES if m[0] == name))
+        modes[name]["full_vs_f64"] = _errors(out.double().cpu().numpy(), f64_full, background)
+        del out
+    line = {"metric": METRIC, "value": modes["f32"]["full_2048x1024x64"]["gcell_steps_per_s"],
+            "unit": UNIT, "n_gpus": 1, "steps": 1, "warmup": 1, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "workload": "precision",
+            "config": {"workload": "precision: rotation_blobs 2048x1024x64, blobs on a 1e-6 "
+                                   "background, periodic x/y, lid z, 100 steps; oracle on a "
+                                   "256x128x64 copy (every 8th cell in x, y)",
+                       "grid": [full.nx, full.ny, full.nz], "oracle_grid": [small.nx, small.ny, small.nz],
+                       "background_threshold": background},
+            "oracle": {"what": what, "threads": threads, "seconds": t_oracle,
+                       "mass_drift": oracle_mass},
+            "modes": modes}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     rank, world, local, dist = dist_init(args)
@@ -383,6 +543,8 @@ def main():
         return run_tracers(args) if rank == 0 else 0
     if args.workload == "serve":
         return run_serve(args) if rank == 0 else 0
+    if args.workload == "precision":
+        return run_precision(args) if rank == 0 else 0
 
     import numpy as np
     import torch
@@ -408,16 +570,17 @@ def main():
     for _ in range(args.warmup):
         solver.step(h, psi, u1, u2, u3, NSTEPS, stream)
     barrier()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
     with ClockSampler(local, enabled=not args.no_clocks) as clk:
         barrier()
-        ev0.record(stream)
-        for _ in range(args.steps):
+        evs[0].record(stream)
+        for s_ in range(args.steps):
             solver.step(h, psi, u1, u2, u3, NSTEPS, stream)
-        ev1.record(stream)
+            evs[s_ + 1].record(stream)
         barrier()
-    ms = max_over_ranks(ev0.elapsed_time(ev1), dist, dev)
+    ms = max_over_ranks(evs[0].elapsed_time(evs[-1]), dist, dev)
     ms_per_step = ms / args.steps
+    per_solve = [evs[i].elapsed_time(evs[i + 1]) for i in range(args.steps)]
     launches = args.steps * NSTEPS
     value = world * ncells * NSTEPS * args.steps / (ms * 1e-3) / 1e9
 
@@ -455,13 +618,14 @@ def main():
             "config": {"workload": "rotation_blobs 1024x512x64, periodic x/y, lid z, "
                                    "50 MPDATA steps per solve",
                        "grid": [NX, NY, NZ], "mpdata_steps_per_step": NSTEPS,
-                       "path": args.path, "tile": list(solver_tile(args, tile)),
+                       "path": args.path, "tile": list(solver.tile),
                        "iterations": 2, "nonoscillatory": True,
                        "l2": "inputs 671 MB + output 134 MB per launch > 129 MB L2 (no flush)",
                        "parallelism": "replicas" if world > 1 else "single"},
             "roofline": roofline, "e2e": e2e, "cpu_baseline": cpu,
             "clocks": clk.summary(), "gpu_launches": launches,
             "pct_hbm_roofline": 100.0 * roofline["frac"],
+            "ci95_pct": ci95_pct(per_solve),
         }
         print(json.dumps(line), flush=True)
     solver.close()
@@ -470,10 +634,20 @@ def main():
     return 0
 
 
-def solver_tile(args, tile):
-    if args.path != "fused":
-        return ()
-    return tile or (32, 16)
+def ci95_pct(samples):
+    """Half-width of the 95 % Student-t confidence interval of the mean, in
+    % of the mean (§6 repeats measurements until the mean is known at 95 %
+    confidence; this bench reports the half-width, 2 % being its target)."""
+    n = len(samples)
+    if n < 2:
+        return None
+    mean = statistics.fmean(samples)
+    try:
+        from scipy.stats import t as student_t
+        q = float(student_t.ppf(0.975, n - 1))
+    except Exception:
+        q = 1.96
+    return 100.0 * q * statistics.stdev(samples) / math.sqrt(n) / mean
 
 
 if __name__ == "__main__":

@@ -222,3 +222,22 @@ def tracer_grid(nx, ny, nz, courant, seed, nsteps=20) -> Fields:
     u1, u2, u3 = constant_courant(nx, ny, nz, courant)
     return Fields("tracer_%dx%dx%d" % (nx, ny, nz), nx, ny, nz, (1, 1, 1),
                   _f32(np.ones(shape)), _f32(psi), u1, u2, u3, nsteps, seed)
+
+
+def precision_grid(nx=2048, ny=1024, nz=64, nsteps=100, seed=1512) -> Fields:
+    """The precision-study grid: rotation_blobs with the blobs on a 1e-6
+    background, so that values span six decades."""
+    f = rotation_blobs(nx=nx, ny=ny, nz=nz, background=1e-6, nsteps=nsteps, seed=seed)
+    return dataclasses.replace(f, name="precision_%dx%dx%d" % (nx, ny, nz))
+
+
+def subsample(f: Fields, every=8, max_c=0.5) -> Fields:
+    """A copy of f every `every`-th cell in x and y (psi and h sampled from
+    f's initial fields, all of z kept) with the rotation field regenerated
+    at the smaller size and the same max |C|."""
+    psi = np.ascontiguousarray(f.psi[:, ::every, ::every])
+    h = np.ascontiguousarray(f.h[:, ::every, ::every])
+    nz, ny, nx = psi.shape
+    u1, u2, u3 = rotation_courant(nx, ny, nz, max_c)
+    return Fields("%s_every%d" % (f.name, every), nx, ny, nz, f.periodic, h, psi, u1, u2, u3,
+                  f.nsteps, f.seed)

@@ -58,15 +58,30 @@ extern "C" {
 #define MPDATA_PATH_FUSED 0  /* all stages of a step in one kernel */
 #define MPDATA_PATH_STAGES 1 /* one kernel per stage, intermediates in HBM */
 
+/* Bounding set of the limiter's local extrema (max/min over a cell and its
+ * six face neighbours, Listing 1 "stage 8"; the set itself follows
+ * Smolarkiewicz & Grabowski 1990). */
+#define MPDATA_EXTREMA_BOTH 0      /* psi^n and the field being corrected (default) */
+#define MPDATA_EXTREMA_CORRECTED 1 /* the field being corrected only */
+
+/* Arithmetic of an FP32 step. */
+#define MPDATA_PREC_PURE 0     /* every operation in the dtype (default) */
+#define MPDATA_PREC_F64_BETA 1 /* FP32 fields; the limiter's in/out flux sums and
+                                  beta factors in FP64 (stage path only) */
+
 typedef struct mpdata_opts {
     uint32_t size;          /* sizeof(mpdata_opts); set by mpdata_opts_default */
-    int32_t iterations;     /* 1: donor cell only; 2: one corrective pass (default) */
+    int32_t iterations;     /* 1: donor cell only; 2: one corrective pass (default);
+                               3: two corrective passes, the second built from the
+                               velocities the first transported with (stage path) */
     int32_t nonoscillatory; /* 1: limit the antidiffusive velocities (default) */
     int32_t periodic[3];    /* per axis x, y, z: 1 periodic (default), 0 rigid lid */
     int32_t dtype;          /* MPDATA_F32 (default) or MPDATA_F64 */
     int32_t path;           /* MPDATA_PATH_FUSED (default) or MPDATA_PATH_STAGES */
     int32_t tile_x, tile_y; /* fused-kernel output tile; 0 picks the default */
     double eps;             /* > 0, added to every A, B and limiter denominator; default 1e-15 */
+    int32_t extrema;        /* MPDATA_EXTREMA_BOTH (default) or _CORRECTED (stage path) */
+    int32_t precision;      /* MPDATA_PREC_PURE (default) or _F64_BETA (FP32, stage path) */
 } mpdata_opts;
 
 typedef struct mpdata_handle mpdata_t;
@@ -78,11 +93,19 @@ void mpdata_opts_default(mpdata_opts *opts);
  * device.  The handle owns one psi-sized device scratch buffer (the step's
  * ping-pong partner) and, for the stage-per-kernel path, the intermediate
  * arrays; they are allocated here and freed by mpdata_destroy.
- * Errors: EINVAL (dims, opts), ENOMEM, ECUDA. */
+ * The fused path implements iterations 1 and 2 with the default extrema set
+ * and pure precision; iterations = 3, MPDATA_EXTREMA_CORRECTED and
+ * MPDATA_PREC_F64_BETA (with MPDATA_F32) need path = MPDATA_PATH_STAGES.
+ * Errors: EINVAL (dims, opts, an option the chosen path lacks), ENOMEM, ECUDA. */
 int mpdata_create(int nx, int ny, int nz, const mpdata_opts *opts, mpdata_t **out);
 
 /* Free the handle and everything it owns (NULL is accepted). */
 int mpdata_destroy(mpdata_t *handle);
+
+/* The fused-kernel output tile the handle runs (the default one when
+ * opts.tile_x = tile_y = 0), written to *tile_x and *tile_y; 0 x 0 for the
+ * stage path.  Errors: EINVAL (NULL argument). */
+int mpdata_get_tile(const mpdata_t *handle, int *tile_x, int *tile_y);
 
 /* Advance psi by nsteps MPDATA steps in place (async on `stream`).
  * h, u1, u2, u3, psi: device pointers to nx*ny*nz elements of the handle's

@@ -17,6 +17,8 @@ from ._lib import MpdataError, check, version  # noqa: F401
 
 _DTYPES = {"f32": _lib.MPDATA_F32, "f64": _lib.MPDATA_F64}
 _PATHS = {"fused": _lib.MPDATA_PATH_FUSED, "stages": _lib.MPDATA_PATH_STAGES}
+_EXTREMA = {"both": _lib.MPDATA_EXTREMA_BOTH, "corrected": _lib.MPDATA_EXTREMA_CORRECTED}
+_PRECISION = {"pure": _lib.MPDATA_PREC_PURE, "f64_beta": _lib.MPDATA_PREC_F64_BETA}
 
 
 def _torch():
@@ -36,7 +38,11 @@ class Solver:
 
     def __init__(self, nx: int, ny: int, nz: int, *, periodic=(1, 1, 1), iterations: int = 2,
                  nonoscillatory: bool = True, dtype: str = "f32", path: str = "fused",
-                 tile=None, eps: float = 1e-15):
+                 tile=None, eps: float = 1e-15, extrema: str = "both", precision: str = "pure"):
+        """extrema: "both" (psi^n and the corrected field) or "corrected";
+        precision: "pure" or "f64_beta" (FP32 fields, FP64 limiter sums).
+        iterations = 3, extrema = "corrected" and precision = "f64_beta" run
+        on path = "stages"."""
         o = _lib.default_opts()
         o.iterations = int(iterations)
         o.nonoscillatory = int(bool(nonoscillatory))
@@ -47,6 +53,8 @@ class Solver:
         if tile is not None:
             o.tile_x, o.tile_y = int(tile[0]), int(tile[1])
         o.eps = float(eps)
+        o.extrema = _EXTREMA[extrema]
+        o.precision = _PRECISION[precision]
         self.nx, self.ny, self.nz = int(nx), int(ny), int(nz)
         self.dtype_name = dtype
         self.opts = o
@@ -101,6 +109,13 @@ class Solver:
                 ptrs.append(ctypes.c_void_p(a.ctypes.data))
         check(_lib.lib.mpdata_solve_host(self._h, *ptrs, int(nsteps), _stream_handle(stream)),
               "mpdata_solve_host")
+
+    @property
+    def tile(self):
+        """(tile_x, tile_y) of the fused kernel this solver runs; (0, 0) on the stage path."""
+        tx, ty = ctypes.c_int(), ctypes.c_int()
+        check(_lib.lib.mpdata_get_tile(self._h, ctypes.byref(tx), ctypes.byref(ty)), "mpdata_get_tile")
+        return (tx.value, ty.value)
 
     def mass(self, h, psi, out=None, stream=None):
         """(sum h*psi, min psi, max psi) as a float64 CUDA tensor of 3 (async)."""

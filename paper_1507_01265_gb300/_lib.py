@@ -26,13 +26,18 @@ MPDATA_F32 = 0
 MPDATA_F64 = 1
 MPDATA_PATH_FUSED = 0
 MPDATA_PATH_STAGES = 1
+MPDATA_EXTREMA_BOTH = 0
+MPDATA_EXTREMA_CORRECTED = 1
+MPDATA_PREC_PURE = 0
+MPDATA_PREC_F64_BETA = 1
 
 
 class Opts(ctypes.Structure):
     _fields_ = [("size", ctypes.c_uint32), ("iterations", ctypes.c_int32),
                 ("nonoscillatory", ctypes.c_int32), ("periodic", ctypes.c_int32 * 3),
                 ("dtype", ctypes.c_int32), ("path", ctypes.c_int32),
-                ("tile_x", ctypes.c_int32), ("tile_y", ctypes.c_int32), ("eps", ctypes.c_double)]
+                ("tile_x", ctypes.c_int32), ("tile_y", ctypes.c_int32), ("eps", ctypes.c_double),
+                ("extrema", ctypes.c_int32), ("precision", ctypes.c_int32)]
 
 
 class ServerOpts(ctypes.Structure):
@@ -71,6 +76,7 @@ def _load():
         "mpdata_opts_default": (None, [ctypes.POINTER(Opts)]),
         "mpdata_create": (I, [I, I, I, ctypes.POINTER(Opts), ctypes.POINTER(H)]),
         "mpdata_destroy": (I, [H]),
+        "mpdata_get_tile": (I, [H, ctypes.POINTER(I), ctypes.POINTER(I)]),
         "mpdata_step": (I, [H, P, P, P, P, P, I, P]),
         "mpdata_solve_host": (I, [H, P, P, P, P, P, I, P]),
         "mpdata_mass": (I, [H, P, P, P, P]),

@@ -58,13 +58,22 @@ bool aligned16(const void *p) { return p && ((uintptr_t)p & 15u) == 0; }
 
 int check_opts(const mpdata_opts *o) {
     if (o->size < sizeof(mpdata_opts)) return fail(MPDATA_EINVAL, "opts.size too small (use mpdata_opts_default)");
-    if (o->iterations != 1 && o->iterations != 2) return fail(MPDATA_EINVAL, "iterations must be 1 or 2");
+    if (o->iterations < 1 || o->iterations > 3) return fail(MPDATA_EINVAL, "iterations must be 1, 2 or 3");
     if (o->nonoscillatory != 0 && o->nonoscillatory != 1) return fail(MPDATA_EINVAL, "nonoscillatory must be 0 or 1");
     for (int d = 0; d < 3; ++d)
         if (o->periodic[d] != 0 && o->periodic[d] != 1) return fail(MPDATA_EINVAL, "periodic[%d] must be 0 or 1", d);
     if (o->dtype != MPDATA_F32 && o->dtype != MPDATA_F64) return fail(MPDATA_EINVAL, "dtype must be MPDATA_F32 or MPDATA_F64");
     if (o->path != MPDATA_PATH_FUSED && o->path != MPDATA_PATH_STAGES) return fail(MPDATA_EINVAL, "unknown path");
     if (!(o->eps > 0.0)) return fail(MPDATA_EINVAL, "eps must be > 0");
+    if (o->extrema != MPDATA_EXTREMA_BOTH && o->extrema != MPDATA_EXTREMA_CORRECTED)
+        return fail(MPDATA_EINVAL, "extrema must be MPDATA_EXTREMA_BOTH or MPDATA_EXTREMA_CORRECTED");
+    if (o->precision != MPDATA_PREC_PURE && o->precision != MPDATA_PREC_F64_BETA)
+        return fail(MPDATA_EINVAL, "precision must be MPDATA_PREC_PURE or MPDATA_PREC_F64_BETA");
+    if (o->path == MPDATA_PATH_FUSED && o->iterations > 1 &&
+        (o->iterations == 3 || o->extrema != MPDATA_EXTREMA_BOTH ||
+         (o->precision != MPDATA_PREC_PURE && o->dtype == MPDATA_F32)))
+        return fail(MPDATA_EINVAL, "the fused kernel runs two passes with the default extrema set in "
+                                   "pure precision; use path = MPDATA_PATH_STAGES for this option");
     return MPDATA_OK;
 }
 
@@ -77,6 +86,10 @@ void free_handle(mpdata_t *m) {
     cudaFree(m->st.v3);
     cudaFree(m->st.bup);
     cudaFree(m->st.bdn);
+    cudaFree(m->st.psi2);
+    cudaFree(m->st.w1);
+    cudaFree(m->st.w2);
+    cudaFree(m->st.w3);
     cudaFree(m->partials);
     for (int f = 0; f < 5; ++f) cudaFree(m->host_fields[f]);
     delete m;
@@ -89,8 +102,8 @@ int launch_one(mpdata_t *m, const void *h, const void *src, const void *u1, cons
     if (o.iterations == 1)
         e = mpdata::launch_donor(o.dtype, m->grid, h, src, u1, u2, u3, dst, s);
     else if (o.path == MPDATA_PATH_STAGES)
-        e = mpdata::launch_stage_step(o.dtype, m->grid, o.iterations, o.nonoscillatory, o.eps, h,
-                                      src, u1, u2, u3, dst, m->st, s);
+        e = mpdata::launch_stage_step(o.dtype, m->grid, o.iterations, o.nonoscillatory, o.extrema,
+                                      o.precision, o.eps, h, src, u1, u2, u3, dst, m->st, s);
     else
         e = mpdata::launch_fused_step(o.dtype, m->grid, o.nonoscillatory, o.eps, m->tile_x,
                                       m->tile_y, h, src, u1, u2, u3, dst, s);
@@ -112,6 +125,8 @@ void mpdata_opts_default(mpdata_opts *o) {
     o->path = MPDATA_PATH_FUSED;
     o->tile_x = o->tile_y = 0;
     o->eps = 1e-15;
+    o->extrema = MPDATA_EXTREMA_BOTH;
+    o->precision = MPDATA_PREC_PURE;
 }
 
 int mpdata_create(int nx, int ny, int nz, const mpdata_opts *opts, mpdata_t **out) {
@@ -147,6 +162,10 @@ int mpdata_create(int nx, int ny, int nz, const mpdata_opts *opts, mpdata_t **ou
     if (e == cudaSuccess && o.path == MPDATA_PATH_STAGES) {
         void **b[6] = {&m->st.psi1, &m->st.v1, &m->st.v2, &m->st.v3, &m->st.bup, &m->st.bdn};
         for (int i = 0; i < 6 && e == cudaSuccess; ++i) e = cudaMalloc(b[i], bytes);
+        if (o.iterations == 3) {
+            void **b3[4] = {&m->st.psi2, &m->st.w1, &m->st.w2, &m->st.w3};
+            for (int i = 0; i < 4 && e == cudaSuccess; ++i) e = cudaMalloc(b3[i], bytes);
+        }
     }
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -160,6 +179,14 @@ int mpdata_create(int nx, int ny, int nz, const mpdata_opts *opts, mpdata_t **ou
 
 int mpdata_destroy(mpdata_t *m) {
     free_handle(m);
+    return MPDATA_OK;
+}
+
+int mpdata_get_tile(const mpdata_t *m, int *tile_x, int *tile_y) {
+    if (!m || !tile_x || !tile_y) return fail(MPDATA_EINVAL, "NULL argument");
+    const bool fused = m->opts.path == MPDATA_PATH_FUSED && m->opts.iterations == 2;
+    *tile_x = fused ? m->tile_x : 0;
+    *tile_y = fused ? m->tile_y : 0;
     return MPDATA_OK;
 }
 

@@ -154,8 +154,10 @@ int mpdata_batch_create(int ngrids, const int *dims, const int *periodic, const 
     mpdata_opts o;
     if (opts) o = *opts; else mpdata_opts_default(&o);
     if (o.size < sizeof(mpdata_opts)) return bfail(MPDATA_EINVAL, "opts.size too small");
-    if (o.dtype != MPDATA_F32 || o.iterations != 2 || o.path != MPDATA_PATH_FUSED)
-        return bfail(MPDATA_EINVAL, "batches run the FP32 fused step with 2 iterations");
+    if (o.dtype != MPDATA_F32 || o.iterations != 2 || o.path != MPDATA_PATH_FUSED ||
+        o.extrema != MPDATA_EXTREMA_BOTH || o.precision != MPDATA_PREC_PURE)
+        return bfail(MPDATA_EINVAL, "batches run the FP32 fused step with 2 iterations, the default "
+                                    "extrema set and pure precision");
     if (!(o.eps > 0.0)) return bfail(MPDATA_EINVAL, "eps must be > 0");
     int tx = o.tile_x ? o.tile_x : 32, ty = o.tile_y ? o.tile_y : 24;
     if (!(tx == 32 && (ty == 16 || ty == 24))) return bfail(MPDATA_EINVAL, "batch tile must be 32x16 or 32x24");

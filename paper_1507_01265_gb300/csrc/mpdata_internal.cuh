@@ -62,14 +62,18 @@ __host__ __device__ inline TileArgs batch_args(const BatchGrid &b, int parity) {
 }
 
 // Launchers of the stage-per-kernel path (mpdata_stages.cu).
+// Intermediates of the stage path; psi2 and w1..w3 (the second corrective
+// pass's pseudo-velocities) only with three passes.
 struct StageBuffers {
     void *psi1, *v1, *v2, *v3, *bup, *bdn;
+    void *psi2, *w1, *w2, *w3;
 };
 cudaError_t launch_donor(int dtype, const Grid &g, const void *h, const void *psi, const void *w1,
                          const void *w2, const void *w3, void *out, cudaStream_t s);
-cudaError_t launch_stage_step(int dtype, const Grid &g, int iterations, int nonosc, double eps,
-                              const void *h, const void *psi, const void *u1, const void *u2,
-                              const void *u3, void *out, const StageBuffers &b, cudaStream_t s);
+cudaError_t launch_stage_step(int dtype, const Grid &g, int iterations, int nonosc, int extrema,
+                              int precision, double eps, const void *h, const void *psi,
+                              const void *u1, const void *u2, const void *u3, void *out,
+                              const StageBuffers &b, cudaStream_t s);
 
 // Fused step.  FP32 grids with nx % 4 == 0 and a pair tile (32x16, 32x24)
 // run the two-columns-per-thread kernel (mpdata_fused2.cu); everything else

@@ -11,6 +11,13 @@
 //              (Listing 1, stage 8) and the in/out antidiffusive fluxes
 //   vmon       V_d limited by beta (in place)
 //   donor      psi^{n+1} = corrective upstream pass of psi1 with V
+//
+// With three passes the last four stages run again on the result psi2 of
+// the first corrective pass, the pseudo-velocities now built from the
+// limited velocities V of that pass (each pass estimates the error of the
+// pass before it).  Options of this path only: the extrema set (psi^n and
+// the corrected field, or the corrected field alone) and, for FP32 fields,
+// FP64 accumulation of the limiter's flux sums and beta factors.
 #include "mpdata_internal.cuh"
 
 namespace mpdata {
@@ -123,40 +130,47 @@ __global__ void k_antidiff(Grid g, T eps, const T *__restrict__ h, const T *__re
     v3[q] = antidiff(g, h, p1, u, eps, 2, c.i, c.j, c.k);
 }
 
-template <typename T>
-__global__ void k_limiter(Grid g, T eps, const T *__restrict__ h, const T *__restrict__ psi,
-                          const T *__restrict__ p1, const T *__restrict__ v1,
-                          const T *__restrict__ v2, const T *__restrict__ v3,
-                          T *__restrict__ bup, T *__restrict__ bdn) {
+// Limiter factors of the pass that corrects p: extrema over the 7-point
+// stencil of p and (extrema == 0) psi^n; the in/out flux sums and the beta
+// ratios are accumulated in Acc (T, or double for the FP64-beta option).
+template <typename T, typename Acc>
+__global__ void k_limiter(Grid g, Acc eps, int extrema, const T *__restrict__ h,
+                          const T *__restrict__ psi, const T *__restrict__ p1,
+                          const T *__restrict__ v1, const T *__restrict__ v2,
+                          const T *__restrict__ v3, T *__restrict__ bup, T *__restrict__ bdn) {
     Cell c;
     if (!this_cell(g, c)) return;
     const int i = c.i, j = c.j, k = c.k;
     const int off[7][3] = {{0, 0, 0}, {-1, 0, 0}, {1, 0, 0}, {0, -1, 0},
                            {0, 1, 0}, {0, 0, -1}, {0, 0, 1}};
-    T mx = at(g, psi, i, j, k), mn = mx;
+    T mx = at(g, p1, i, j, k), mn = mx;
 #pragma unroll
     for (int n = 0; n < 7; ++n) {
-        T a = at(g, psi, i + off[n][0], j + off[n][1], k + off[n][2]);
         T b = at(g, p1, i + off[n][0], j + off[n][1], k + off[n][2]);
-        mx = fmax(mx, fmax(a, b));
-        mn = fmin(mn, fmin(a, b));
+        mx = fmax(mx, b);
+        mn = fmin(mn, b);
+        if (extrema == 0) {
+            T a = at(g, psi, i + off[n][0], j + off[n][1], k + off[n][2]);
+            mx = fmax(mx, a);
+            mn = fmin(mn, a);
+        }
     }
     const T *v[3] = {v1, v2, v3};
-    T pc = at(g, p1, i, j, k);
-    T in = T(0), out = T(0);
+    const T pc = at(g, p1, i, j, k);
+    Acc in = Acc(0), out = Acc(0);
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
         int e[3] = {0, 0, 0};
         e[d] = 1;
-        T vlo = face(g, v[d], d, i, j, k);
-        T vhi = face(g, v[d], d, i + e[0], j + e[1], k + e[2]);
-        in += fmax(vlo, T(0)) * at(g, p1, i - e[0], j - e[1], k - e[2]) -
-              fmin(vhi, T(0)) * at(g, p1, i + e[0], j + e[1], k + e[2]);
-        out += fmax(vhi, T(0)) * pc - fmin(vlo, T(0)) * pc;
+        const Acc vlo = face(g, v[d], d, i, j, k);
+        const Acc vhi = face(g, v[d], d, i + e[0], j + e[1], k + e[2]);
+        in += fmax(vlo, Acc(0)) * Acc(at(g, p1, i - e[0], j - e[1], k - e[2])) -
+              fmin(vhi, Acc(0)) * Acc(at(g, p1, i + e[0], j + e[1], k + e[2]));
+        out += fmax(vhi, Acc(0)) * Acc(pc) - fmin(vlo, Acc(0)) * Acc(pc);
     }
-    T hc = h[lin(g, i, j, k)];
-    bup[lin(g, i, j, k)] = (mx - pc) * hc / (in + eps);
-    bdn[lin(g, i, j, k)] = (pc - mn) * hc / (out + eps);
+    const Acc hc = h[lin(g, i, j, k)];
+    bup[lin(g, i, j, k)] = T((Acc(mx) - Acc(pc)) * hc / (in + eps));
+    bdn[lin(g, i, j, k)] = T((Acc(pc) - Acc(mn)) * hc / (out + eps));
 }
 
 template <typename T>
@@ -197,27 +211,48 @@ cudaError_t donor_t(const Grid &g, const void *h, const void *psi, const void *w
     return cudaGetLastError();
 }
 
+// One corrective pass: antidiffusive velocities of the field p (made with
+// the face velocities w) into v, limiter (in place on v), corrective donor
+// pass of p with v into out.
 template <typename T>
-cudaError_t stage_step_t(const Grid &g, int iterations, int nonosc, double eps, const void *h,
-                         const void *psi, const void *u1, const void *u2, const void *u3,
-                         void *out, const StageBuffers &b, cudaStream_t s) {
+void corrective_pass_t(const Grid &g, int nonosc, int extrema, int precision, double eps,
+                       const T *h, const T *psi, const T *p, const T *const w[3], T *const v[3],
+                       T *bup, T *bdn, T *out, cudaStream_t s) {
+    dim3 gr = grid_of(g);
+    k_antidiff<T><<<gr, kBlockX, 0, s>>>(g, (T)eps, h, p, w[0], w[1], w[2], v[0], v[1], v[2]);
+    if (nonosc) {
+        if (precision == MPDATA_PREC_F64_BETA)
+            k_limiter<T, double><<<gr, kBlockX, 0, s>>>(g, eps, extrema, h, psi, p, v[0], v[1],
+                                                        v[2], bup, bdn);
+        else
+            k_limiter<T, T><<<gr, kBlockX, 0, s>>>(g, (T)eps, extrema, h, psi, p, v[0], v[1], v[2],
+                                                   bup, bdn);
+        k_vmon<T><<<gr, kBlockX, 0, s>>>(g, bup, bdn, v[0], v[1], v[2]);
+    }
+    k_donor<T><<<gr, kBlockX, 0, s>>>(g, h, p, v[0], v[1], v[2], out);
+}
+
+template <typename T>
+cudaError_t stage_step_t(const Grid &g, int iterations, int nonosc, int extrema, int precision,
+                         double eps, const void *h, const void *psi, const void *u1,
+                         const void *u2, const void *u3, void *out, const StageBuffers &b,
+                         cudaStream_t s) {
     if (iterations <= 1) return donor_t<T>(g, h, psi, u1, u2, u3, out, s);
     dim3 gr = grid_of(g);
-    const T *H = (const T *)h;
-    k_donor<T><<<gr, kBlockX, 0, s>>>(g, H, (const T *)psi, (const T *)u1, (const T *)u2,
-                                       (const T *)u3, (T *)b.psi1);
-    k_antidiff<T><<<gr, kBlockX, 0, s>>>(g, (T)eps, H, (const T *)b.psi1, (const T *)u1,
-                                          (const T *)u2, (const T *)u3, (T *)b.v1, (T *)b.v2,
-                                          (T *)b.v3);
-    if (nonosc) {
-        k_limiter<T><<<gr, kBlockX, 0, s>>>(g, (T)eps, H, (const T *)psi, (const T *)b.psi1,
-                                             (const T *)b.v1, (const T *)b.v2, (const T *)b.v3,
-                                             (T *)b.bup, (T *)b.bdn);
-        k_vmon<T><<<gr, kBlockX, 0, s>>>(g, (const T *)b.bup, (const T *)b.bdn, (T *)b.v1,
-                                          (T *)b.v2, (T *)b.v3);
+    const T *H = (const T *)h, *P = (const T *)psi;
+    k_donor<T><<<gr, kBlockX, 0, s>>>(g, H, P, (const T *)u1, (const T *)u2, (const T *)u3,
+                                       (T *)b.psi1);
+    const T *const w[3] = {(const T *)u1, (const T *)u2, (const T *)u3};
+    T *const v[3] = {(T *)b.v1, (T *)b.v2, (T *)b.v3};
+    T *pass2 = iterations == 2 ? (T *)out : (T *)b.psi2;
+    corrective_pass_t<T>(g, nonosc, extrema, precision, eps, H, P, (const T *)b.psi1, w, v,
+                         (T *)b.bup, (T *)b.bdn, pass2, s);
+    if (iterations == 3) {
+        const T *const wv[3] = {v[0], v[1], v[2]};
+        T *const v3[3] = {(T *)b.w1, (T *)b.w2, (T *)b.w3};
+        corrective_pass_t<T>(g, nonosc, extrema, precision, eps, H, P, (const T *)b.psi2, wv, v3,
+                             (T *)b.bup, (T *)b.bdn, (T *)out, s);
     }
-    k_donor<T><<<gr, kBlockX, 0, s>>>(g, H, (const T *)b.psi1, (const T *)b.v1, (const T *)b.v2,
-                                       (const T *)b.v3, (T *)out);
     return cudaGetLastError();
 }
 
@@ -229,12 +264,15 @@ cudaError_t launch_donor(int dtype, const Grid &g, const void *h, const void *ps
                                : donor_t<float>(g, h, psi, w1, w2, w3, out, s);
 }
 
-cudaError_t launch_stage_step(int dtype, const Grid &g, int iterations, int nonosc, double eps,
-                              const void *h, const void *psi, const void *u1, const void *u2,
-                              const void *u3, void *out, const StageBuffers &b, cudaStream_t s) {
+cudaError_t launch_stage_step(int dtype, const Grid &g, int iterations, int nonosc, int extrema,
+                              int precision, double eps, const void *h, const void *psi,
+                              const void *u1, const void *u2, const void *u3, void *out,
+                              const StageBuffers &b, cudaStream_t s) {
     return dtype == MPDATA_F64
-               ? stage_step_t<double>(g, iterations, nonosc, eps, h, psi, u1, u2, u3, out, b, s)
-               : stage_step_t<float>(g, iterations, nonosc, eps, h, psi, u1, u2, u3, out, b, s);
+               ? stage_step_t<double>(g, iterations, nonosc, extrema, precision, eps, h, psi, u1,
+                                      u2, u3, out, b, s)
+               : stage_step_t<float>(g, iterations, nonosc, extrema, precision, eps, h, psi, u1,
+                                     u2, u3, out, b, s);
 }
 
 }  // namespace mpdata

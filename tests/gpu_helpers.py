@@ -27,7 +27,7 @@ def rand_problem(shape, seed, umax=0.12, periodic=(1, 1, 1), hvar=True):
 
 
 def run_gpu(f: F.Fields, nsteps, dtype="f32", path="fused", iterations=2, nonosc=True,
-            tile=None, psi=None):
+            tile=None, psi=None, extrema="both", precision="pure"):
     import torch
     import paper_1507_01265_gb300 as mp
     td = torch.float64 if dtype == "f64" else torch.float32
@@ -35,14 +35,16 @@ def run_gpu(f: F.Fields, nsteps, dtype="f32", path="fused", iterations=2, nonosc
     arrs = [f.h, f.psi if psi is None else psi, f.u1, f.u2, f.u3]
     t = [torch.from_numpy(np.ascontiguousarray(a)).to(dev, td) for a in arrs]
     with mp.Solver(f.nx, f.ny, f.nz, periodic=f.periodic, iterations=iterations,
-                   nonoscillatory=nonosc, dtype=dtype, path=path, tile=tile) as s:
+                   nonoscillatory=nonosc, dtype=dtype, path=path, tile=tile, extrema=extrema,
+                   precision=precision) as s:
         s.step(t[0], t[1], t[2], t[3], t[4], nsteps)
         torch.cuda.synchronize()
     return t[1].double().cpu().numpy()
 
 
-def run_oracle(f: F.Fields, nsteps, iterations=2, nonosc=True):
-    cfg = oracle.Config(f.nx, f.ny, f.nz, tuple(f.periodic), iterations, int(nonosc))
+def run_oracle(f: F.Fields, nsteps, iterations=2, nonosc=True, extrema="both"):
+    cfg = oracle.Config(f.nx, f.ny, f.nz, tuple(f.periodic), iterations, int(nonosc), 1e-15,
+                        {"both": 0, "corrected": 1}[extrema])
     return oracle.run(cfg, *f.as_f64(), nsteps=nsteps)
 
 

@@ -44,6 +44,17 @@ def test_defaults(mp):
     assert o.size == ctypes.sizeof(mp._lib.Opts)
     assert (o.iterations, o.nonoscillatory, tuple(o.periodic), o.dtype, o.path) == (2, 1, (1, 1, 1), 0, 0)
     assert o.eps == 1e-15
+    assert (o.extrema, o.precision) == (mp._lib.MPDATA_EXTREMA_BOTH, mp._lib.MPDATA_PREC_PURE)
+
+
+def test_header_constants_match_binding(mp):
+    """Every #define MPDATA_* of the header has the same value in the binding."""
+    text = open(os.path.join(ROOT, "include", "mpdata.h")).read()
+    defs = dict(re.findall(r"#define\s+(MPDATA_[A-Z0-9_]+)\s+\(?(-?\d+)\)?", text))
+    assert len(defs) >= 20
+    for name, value in defs.items():
+        bound = getattr(mp._lib, name, getattr(mp._lib, name[len("MPDATA_"):], None))
+        assert bound == int(value), name
 
 
 def test_invalid_arguments_without_gpu(mp):
@@ -52,8 +63,20 @@ def test_invalid_arguments_without_gpu(mp):
     o = L.default_opts()
     assert L.lib.mpdata_create(0, 4, 4, ctypes.byref(o), ctypes.byref(h)) == L.MPDATA_EINVAL
     assert "dims" in L.last_error_message()
-    o.iterations = 3
+    o.iterations = 4
     assert L.lib.mpdata_create(4, 4, 4, ctypes.byref(o), ctypes.byref(h)) == L.MPDATA_EINVAL
+    # options the fused kernel lacks are refused on the fused path
+    for field, value in (("iterations", 3), ("extrema", L.MPDATA_EXTREMA_CORRECTED),
+                         ("precision", L.MPDATA_PREC_F64_BETA)):
+        o = L.default_opts()
+        setattr(o, field, value)
+        assert L.lib.mpdata_create(4, 4, 4, ctypes.byref(o), ctypes.byref(h)) == L.MPDATA_EINVAL
+        assert "MPDATA_PATH_STAGES" in L.last_error_message()
+    for field in ("extrema", "precision"):
+        o = L.default_opts()
+        o.path = L.MPDATA_PATH_STAGES
+        setattr(o, field, 2)
+        assert L.lib.mpdata_create(4, 4, 4, ctypes.byref(o), ctypes.byref(h)) == L.MPDATA_EINVAL
     o = L.default_opts()
     o.eps = 0.0
     assert L.lib.mpdata_create(4, 4, 4, ctypes.byref(o), ctypes.byref(h)) == L.MPDATA_EINVAL

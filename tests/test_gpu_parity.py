@@ -95,6 +95,64 @@ def test_donor_only(dtype):
     assert rel_err(got, want) <= (1e-5 if dtype == "f32" else 1e-12)
 
 
+# ---- stage-path options: three passes, extrema set, FP64 limiter sums -------------------
+
+OPTION_SHAPES = [(37, 23, 11, (1, 1, 1)), (9, 40, 7, (0, 1, 0)), (64, 32, 16, (0, 0, 0)),
+                 (5, 3, 2, (1, 1, 1)), (33, 17, 20, (1, 1, 0))]
+OPTIONS = [(3, "both"), (3, "corrected"), (2, "corrected")]
+
+
+@pytest.mark.parametrize("nx,ny,nz,per", OPTION_SHAPES)
+@pytest.mark.parametrize("iterations,extrema", OPTIONS)
+@pytest.mark.parametrize("nonosc", [True, False])
+def test_stage_options_f64(nx, ny, nz, per, iterations, extrema, nonosc):
+    f = rand_problem((nz, ny, nx), seed=nx * 7 + ny * 3 + nz, periodic=per)
+    want = run_oracle(f, 3, iterations=iterations, nonosc=nonosc, extrema=extrema)
+    got = run_gpu(f, 3, dtype="f64", path="stages", iterations=iterations, nonosc=nonosc,
+                  extrema=extrema)
+    assert rel_err(got, want) <= 1e-12
+
+
+@pytest.mark.parametrize("nx,ny,nz,per", OPTION_SHAPES)
+@pytest.mark.parametrize("iterations,extrema", OPTIONS)
+@pytest.mark.parametrize("precision", ["pure", "f64_beta"])
+def test_stage_options_f32(nx, ny, nz, per, iterations, extrema, precision):
+    f = rand_problem((nz, ny, nx), seed=nx * 11 + ny * 5 + nz, periodic=per)
+    want = run_oracle(f, 3, iterations=iterations, extrema=extrema)
+    got = run_gpu(f, 3, path="stages", iterations=iterations, extrema=extrema, precision=precision)
+    assert rel_err(got, want) <= 1e-5
+
+
+@pytest.mark.parametrize("iterations", [2, 3])
+def test_f64_beta_gaussian_constant_100_steps(iterations):
+    f = F.gaussian_constant()
+    got = run_gpu(f, 100, path="stages", iterations=iterations, precision="f64_beta")
+    want = run_oracle(f, 100, iterations=iterations)
+    assert rel_err(got, want) <= 1e-4
+
+
+def test_f64_beta_is_a_no_op_for_f64():
+    f = rand_problem((6, 20, 24), seed=41, periodic=(1, 1, 0))
+    a = run_gpu(f, 3, dtype="f64", path="stages", precision="f64_beta")
+    b = run_gpu(f, 3, dtype="f64", path="stages")
+    assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+def test_three_passes_shift_exact(dtype):
+    shape = (5, 12, 17)
+    r = np.random.default_rng(12)
+    psi = r.integers(1, 2 ** 20, size=shape).astype(np.float32)
+    for axis in range(3):
+        u = [np.zeros(shape, np.float32) for _ in range(3)]
+        u[axis][:] = -1.0
+        f = F.Fields("shift3", shape[2], shape[1], shape[0], (1, 1, 1),
+                     np.ones(shape, np.float32), psi, u[0], u[1], u[2], 2, 0)
+        for extrema in ("both", "corrected"):
+            got = run_gpu(f, 2, dtype=dtype, path="stages", iterations=3, extrema=extrema)
+            assert np.array_equal(got, np.roll(psi.astype(np.float64), -2, axis=2 - axis))
+
+
 # ---- exact cases ------------------------------------------------------------------------
 
 @pytest.mark.parametrize("dtype", ["f32", "f64"])
