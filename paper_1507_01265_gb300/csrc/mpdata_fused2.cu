@@ -71,15 +71,18 @@ __device__ __forceinline__ void st2(float *p, F2 v) { *reinterpret_cast<F2 *>(p)
 
 // Pseudo-velocity of both faces of the pair (see mpdata_fused.cu):
 //   V = (|U| - U^2/hbar) A - U (Ubar_a B_a + Ubar_b B_b) / hbar
-__device__ __forceinline__ F2 pseudo_velocity(F2 U, F2 pR, F2 pL, F2 spa, F2 sma, F2 ua, F2 spb,
-                                              F2 smb, F2 ub, F2 hsum, F2 eps) {
-    const F2 A = mul(sub(pR, pL), rcp(add(add(pR, pL), eps)));
+__device__ __forceinline__ F2 pseudo_velocity(F2 U, F2 pR, F2 pL, F2 psum, F2 spa, F2 sma, F2 ua,
+                                              F2 spb, F2 smb, F2 ub, F2 hsum, F2 eps) {
+    const F2 A = mul(sub(pR, pL), rcp(add(psum, eps)));
     const F2 Ba = mul(sub(spa, sma), rcp(add(add(spa, sma), eps)));
     const F2 Bb = mul(sub(spb, smb), rcp(add(add(spb, smb), eps)));
-    const F2 r = mul(bc(2.f), rcp(hsum));                     // 1/hbar
-    const F2 cross = mul(bc(0.125f), fma2(ua, Ba, mul(ub, Bb)));  // 1/4 (Ubar) x 1/2 (B)
-    const F2 t = mul(U, r);
-    return sub(mul(sub(fabs2(U), mul(U, t)), A), mul(t, cross));
+    // t = U / hbar = 2U / hsum; the 1/4 (Ubar) x 1/2 (B) of the cross term
+    // rides on t/8.  The power-of-two scalings are exact, so this is the
+    // same value as scaling after the reciprocal, one step shorter.
+    const F2 rh = rcp(hsum);
+    const F2 t = mul(add(U, U), rh);
+    const F2 t8 = mul(mul(bc(0.25f), U), rh);
+    return sub(mul(sub(fabs2(U), mul(U, t)), A), mul(t8, fma2(ua, Ba, mul(ub, Bb))));
 }
 
 template <int TX, int TY>
@@ -319,7 +322,7 @@ __device__ __forceinline__ void pairs_tile(const TileArgs &a, int tile, float *s
                 const F2 ua = add(add(add(lshF(r2 + 2 * FB, u2b), u2b),
                                       make_float2(lds<2 * FB + RB - 4>(r2), u2U.x)), u2U);
                 const F2 ub = add(add(add(lshF(r2 + 3 * FB, u3b), u3b), lshF(r1 + 3 * FB, u3c)), u3c);
-                const F2 v = pseudo_velocity(u1b, p1b, pl, ldU(b2 + oSX), ldD(b2 + oSX), ua, sxc, sxa,
+                const F2 v = pseudo_velocity(u1b, p1b, pl, sxb, ldU(b2 + oSX), ldD(b2 + oSX), ua, sxc, sxa,
                                              ub, add(lshF(r2 + 4 * FB, hb), hb), eps);
                 v1_own = LID ? lid2(v, xlid0, xlid1) : v;
             }
@@ -328,7 +331,7 @@ __device__ __forceinline__ void pairs_tile(const TileArgs &a, int tile, float *s
                 const F2 va = add(add(add(ldp<3 * FB - RB>(r2), u3b), ldp<3 * FB - RB>(r1)), u3c);
                 const F2 vb = add(add(add(u1D, u1b), make_float2(u1D.y, lds<FB - RB + 8>(r2))),
                                   rshF(r2 + FB, u1b));
-                const F2 v = pseudo_velocity(u2b, p1b, pd, syc, sya, va, rshC(b2 + oSY, syb),
+                const F2 v = pseudo_velocity(u2b, p1b, pd, syb, syc, sya, va, rshC(b2 + oSY, syb),
                                              lshC(b2 + oSY, syb), vb, add(ldp<4 * FB - RB>(r2), hb), eps);
                 v2_own = (LID && ylid) ? Z : v;
             }
@@ -344,7 +347,7 @@ __device__ __forceinline__ void pairs_tile(const TileArgs &a, int tile, float *s
                 const F2 szo = add(p1b, p1c);
                 const F2 ua = add(add(add(u1b, u1c), rshF(r2 + FB, u1b)), rshF(r1 + FB, u1c));
                 const F2 ub = add(add(add(u2b, u2c), ldp<2 * FB + RB>(r2)), ldp<2 * FB + RB>(r1));
-                whi_v = pseudo_velocity(u3c, p1c, p1b, rshC(tb + oSZ, szo), lshC(tb + oSZ, szo), ua,
+                whi_v = pseudo_velocity(u3c, p1c, p1b, szo, rshC(tb + oSZ, szo), lshC(tb + oSZ, szo), ua,
                                         ldU(tb + oSZ), ldD(tb + oSZ), ub, add(hb, hc), eps);
             }
             if (NONOSC && q2 >= vlo && q2 <= vhi) {
