@@ -131,6 +131,18 @@ int mpdata_solve_host(mpdata_t *handle, const void *h, void *psi, const void *u1
  * Errors: EINVAL, ECUDA. */
 int mpdata_mass(mpdata_t *handle, const void *h, const void *psi, void *out3, void *stream);
 
+/* Stability check (async): the largest outflow Courant number over all
+ * cells, max_c sum_d ([U_d(c + e_d)]+ - [U_d(c)]-) / h_c, with the handle's
+ * boundary conditions (lid faces carry no velocity).  The donor-cell pass
+ * keeps psi >= 0 -- and the scheme is stable -- only while it is <= 1; the
+ * library does not check it on every step, the caller does.  Written as
+ * three doubles to the DEVICE pointer out3: out3[1] = out3[2] = the maximum
+ * (out3[0] = 0), computed in FP64 with a fixed reduction tree.
+ * h, u1, u2, u3: device pointers (16-byte aligned) of the handle's dtype.
+ * Errors: EINVAL, ECUDA. */
+int mpdata_courant_max(mpdata_t *handle, const void *h, const void *u1, const void *u2,
+                       const void *u3, void *out3, void *stream);
+
 /* mpdata_mass without a handle and without any device allocation, for
  * callers that cannot allocate device memory themselves: code embedded in a
  * host framework whose allocator owns all device memory and forbids raw

@@ -127,6 +127,17 @@ class Solver:
               "mpdata_mass")
         return out
 
+    def courant_max(self, h, u1, u2, u3, stream=None) -> float:
+        """Largest outflow Courant number over all cells (the donor pass keeps
+        psi >= 0 while it is <= 1); waits for the result."""
+        torch = _torch()
+        out = torch.empty(3, dtype=torch.float64, device=h.device)
+        check(_lib.lib.mpdata_courant_max(self._h, self._dev(h, "h"), self._dev(u1, "u1"),
+                                          self._dev(u2, "u2"), self._dev(u3, "u3"),
+                                          ctypes.c_void_p(out.data_ptr()), _stream_handle(stream)),
+              "mpdata_courant_max")
+        return float(out[2].item())
+
     def close(self) -> None:
         if getattr(self, "_h", None) is not None and self._h.value:
             _lib.lib.mpdata_destroy(self._h)

@@ -257,6 +257,19 @@ int mpdata_mass(mpdata_t *m, const void *h, const void *psi, void *out3, void *s
     return e == cudaSuccess ? MPDATA_OK : cuda_fail(e, "mass kernel launch");
 }
 
+int mpdata_courant_max(mpdata_t *m, const void *h, const void *u1, const void *u2, const void *u3,
+                       void *out3, void *stream) {
+    if (!m) return fail(MPDATA_EINVAL, "handle is NULL");
+    const void *ptrs[4] = {h, u1, u2, u3};
+    const char *names[4] = {"h", "u1", "u2", "u3"};
+    for (int f = 0; f < 4; ++f)
+        if (!aligned16(ptrs[f])) return fail(MPDATA_EINVAL, "%s is NULL or not 16-byte aligned", names[f]);
+    if (!out3 || ((uintptr_t)out3 & 7u)) return fail(MPDATA_EINVAL, "out3 is NULL or not 8-byte aligned");
+    cudaError_t e = mpdata::launch_courant_max(m->opts.dtype, m->grid, h, u1, u2, u3, m->partials,
+                                               (double *)out3, (cudaStream_t)stream);
+    return e == cudaSuccess ? MPDATA_OK : cuda_fail(e, "courant kernel launch");
+}
+
 int mpdata_mass_noalloc(const void *h, const void *psi, long long n, int dtype, void *out3,
                         void *stream) {
     if (n < 1 || n >= (1LL << 31))

@@ -105,5 +105,9 @@ cudaError_t launch_mass(int dtype, long long n, const void *h, const void *psi, 
 // Device address of the static partials array of mpdata_mass_noalloc on the
 // current device (looked up on the first call per device).
 cudaError_t noalloc_partials(double **out);
+// out3[2] (and out3[1]) = max over cells of the outflow Courant number.
+cudaError_t launch_courant_max(int dtype, const Grid &g, const void *h, const void *u1,
+                               const void *u2, const void *u3, double *partials, double *out3,
+                               cudaStream_t s);
 
 }  // namespace mpdata

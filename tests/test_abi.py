@@ -84,6 +84,7 @@ def test_invalid_arguments_without_gpu(mp):
     o.tile_x, o.tile_y = 7, 9
     assert L.lib.mpdata_create(4, 4, 4, ctypes.byref(o), ctypes.byref(h)) == L.MPDATA_EINVAL
     assert L.lib.mpdata_step(None, None, None, None, None, None, 1, None) == L.MPDATA_EINVAL
+    assert L.lib.mpdata_courant_max(None, None, None, None, None, None, None) == L.MPDATA_EINVAL
     assert L.lib.mpdata_destroy(None) == L.MPDATA_OK
 
 

@@ -267,3 +267,53 @@ def test_rotation_blobs_full_size_invariants():
         m1 = s.mass(t[0], t[1]).cpu().numpy()
     assert abs(m1[0] / m0[0] - 1) <= 1e-5
     assert m1[1] >= m0[1] - 1e-6 * m0[2] and m1[2] <= m0[2] * (1 + 1e-6)
+
+
+# ---- stability diagnostic ----------------------------------------------------------------
+
+def _outflow_courant_max(f, periodic):
+    """max_c sum_d ([U_d(c + e_d)]+ - [U_d(c)]-) / h_c written out with numpy;
+    lid faces (index 0 and n on a lid axis) carry no velocity."""
+    out = np.zeros((f.nz, f.ny, f.nx))
+    for d, u in enumerate((f.u1, f.u2, f.u3)):
+        a = 2 - d
+        u = u.astype(np.float64)
+        lower, upper = u.copy(), np.roll(u, -1, axis=a)
+        if not periodic[d]:
+            n = u.shape[a]
+            lower[tuple(slice(0, 1) if x == a else slice(None) for x in range(3))] = 0.0
+            upper[tuple(slice(n - 1, n) if x == a else slice(None) for x in range(3))] = 0.0
+        out += np.maximum(upper, 0.0) - np.minimum(lower, 0.0)
+    return float((out / f.h.astype(np.float64)).max())
+
+
+@pytest.mark.parametrize("per", [(1, 1, 1), (1, 1, 0), (0, 1, 1), (0, 0, 0)])
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+def test_courant_max(per, dtype):
+    import torch
+    import paper_1507_01265_gb300 as mp
+    f = rand_problem((7, 19, 33), seed=61, umax=0.3, periodic=per)
+    td = torch.float64 if dtype == "f64" else torch.float32
+    t = [torch.from_numpy(a).to("cuda", td) for a in (f.h, f.u1, f.u2, f.u3)]
+    with mp.Solver(f.nx, f.ny, f.nz, periodic=per, dtype=dtype) as s:
+        got = s.courant_max(*t)
+    assert got == pytest.approx(_outflow_courant_max(f, per), rel=1e-15, abs=0)
+
+
+def test_courant_max_closed_forms():
+    import torch
+    import paper_1507_01265_gb300 as mp
+    # constant Courant vector, h = 1: every cell moves sum_d |C_d| out
+    nx, ny, nz = 24, 10, 6
+    u = F.constant_courant(nx, ny, nz, (0.25, -0.125, 0.5))
+    h = np.ones((nz, ny, nx), np.float32)
+    t = [torch.from_numpy(a).cuda() for a in (h,) + u]
+    with mp.Solver(nx, ny, nz) as s:
+        assert s.courant_max(*t) == 0.875
+    # with lids on z, the top cells have no upper z-face: still 0.875 elsewhere,
+    # and a field whose only velocity sits on the lid faces gives 0
+    uz = [np.zeros((nz, ny, nx), np.float32) for _ in range(3)]
+    uz[2][0] = 0.7
+    t = [torch.from_numpy(a).cuda() for a in [h] + uz]
+    with mp.Solver(nx, ny, nz, periodic=(1, 1, 0)) as s:
+        assert s.courant_max(*t) == 0.0
