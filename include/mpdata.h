@@ -89,8 +89,11 @@ typedef struct mpdata_handle mpdata_t;
 /* Fill *opts with the defaults listed above. */
 void mpdata_opts_default(mpdata_opts *opts);
 
-/* Create a solver for an nx x ny x nz grid (each >= 1) on the current CUDA
- * device.  The handle owns one psi-sized device scratch buffer (the step's
+/* Create a solver for an nx x ny x nz grid on the current CUDA device.
+ * Limits: each dimension >= 1, ny and nz <= 65535, nx * ny < 2^31 (one
+ * z-plane), nx * ny * nz < 2^40 (beyond 2^31 cells the grid is addressed
+ * with 64-bit plane offsets; device memory is the practical limit: 6 fields
+ * of 4 or 8 bytes per cell).  The handle owns one psi-sized device scratch buffer (the step's
  * ping-pong partner) and, for the stage-per-kernel path, the intermediate
  * arrays; they are allocated here and freed by mpdata_destroy.
  * The fused path implements iterations 1 and 2 with the default extrema set

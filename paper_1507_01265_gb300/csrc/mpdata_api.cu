@@ -134,7 +134,9 @@ int mpdata_create(int nx, int ny, int nz, const mpdata_opts *opts, mpdata_t **ou
     *out = nullptr;
     if (nx < 1 || ny < 1 || nz < 1) return fail(MPDATA_EINVAL, "dims must be >= 1 (got %d x %d x %d)", nx, ny, nz);
     long long n = (long long)nx * ny * nz;
-    if (n >= (1LL << 31)) return fail(MPDATA_EINVAL, "grid of %lld cells is too large (limit 2^31 - 1)", n);
+    // in-plane offsets are 32-bit, plane offsets 64-bit
+    if ((long long)nx * ny >= (1LL << 31)) return fail(MPDATA_EINVAL, "nx * ny = %lld: one z-plane must hold fewer than 2^31 cells", (long long)nx * ny);
+    if (n >= (1LL << 40)) return fail(MPDATA_EINVAL, "grid of %lld cells is too large (limit 2^40 - 1)", n);
     if (ny > 65535 || nz > 65535) return fail(MPDATA_EINVAL, "ny and nz must be <= 65535");
     mpdata_opts o;
     if (opts) o = *opts; else mpdata_opts_default(&o);
