@@ -272,19 +272,40 @@ def run_tracers(args):
     nsteps = 20
     stream = torch.cuda.current_stream()
     res = {}
-    with mp.Batch([(f.nx, f.ny, f.nz, f.periodic) for f in fs]) as b:
-        for i, t in enumerate(ts):
-            b.set_fields(i, *t)
-        for _ in range(args.warmup):
-            b.step(nsteps, graph=True)
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(args.steps):
-            b.step(nsteps, graph=True)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        res["batched"] = e0.elapsed_time(e1) / args.steps
+
+    def time_batch(idx, **kw):
+        """ms per bench step of a batch of the grids idx (graph replay)."""
+        with mp.Batch([(fs[i].nx, fs[i].ny, fs[i].nz, fs[i].periodic) for i in idx], **kw) as b:
+            for k, i in enumerate(idx):
+                b.set_fields(k, *ts[i])
+            for _ in range(args.warmup):
+                b.step(nsteps, graph=True)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(args.steps):
+                b.step(nsteps, graph=True)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            return e0.elapsed_time(e1) / args.steps
+
+    every = list(range(len(fs)))
+    res["batched"] = time_batch(every)
+    # per-grid tile shapes (two-column grids only; the others run the
+    # one-column kernel whatever the tile): per-shape rates measured on the
+    # two-column grids, then each grid's shape of least predicted cost
+    from paper_1507_01265_gb300 import tune
+    pairs = [i for i in every if fs[i].nx % 4 == 0]
+    rates = {}
+    for ty in (24, 16):
+        ms = time_batch(pairs, tile=(32, ty))
+        work = sum(math.ceil(fs[i].nx / 32) * math.ceil(fs[i].ny / ty) * 32 * ty * (fs[i].nz + 3)
+                   for i in pairs)
+        rates[ty] = work * nsteps / (ms * 1e-3)
+    nsm = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    chosen = dict(zip(pairs, tune.choose_tiles([(fs[i].nx, fs[i].ny, fs[i].nz) for i in pairs], rates, nsm)))
+    tiles = [chosen.get(i, 0) for i in every]
+    res["per_grid_tiles"] = time_batch(every, tiles=tiles)
     solvers = [mp.Solver(f.nx, f.ny, f.nz, periodic=f.periodic) for f in fs]
     for _ in range(args.warmup):
         for s_, t in zip(solvers, ts):
@@ -309,7 +330,13 @@ def run_tracers(args):
                        "cells": cells, "mpdata_steps_per_step": nsteps},
             "per_grid_launches": {"value": cells * nsteps / (res["per_grid"] * 1e-3) / 1e9,
                                   "ms_per_step": res["per_grid"]},
-            "speedup_vs_per_grid": res["per_grid"] / res["batched"]}
+            "speedup_vs_per_grid": res["per_grid"] / res["batched"],
+            "per_grid_tiles": {"value": cells * nsteps / (res["per_grid_tiles"] * 1e-3) / 1e9,
+                               "ms_per_step": res["per_grid_tiles"],
+                               "two_column_grids": len(pairs),
+                               "tile_y_counts": {str(ty): sum(1 for i in pairs if chosen[i] == ty)
+                                                 for ty in (24, 16)},
+                               "rates_cell_planes_per_s": {str(k): v for k, v in rates.items()}}}
     print(json.dumps(line), flush=True)
     return 0
 

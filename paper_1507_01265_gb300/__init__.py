@@ -161,10 +161,14 @@ class Batch:
     (mpdata_batch_*).  `grids` is a list of (nx, ny, nz) or (nx, ny, nz,
     (px, py, pz)); fields are attached per grid with set_fields."""
 
-    VARIANTS = 3  # 0: two-column periodic x/y, 1: two-column with a lid, 2: one-column
+    # 0/1: two-column 32x24 (x/y periodic / a lid), 2: one-column 32x16,
+    # 3/4: two-column 32x16 (x/y periodic / a lid)
+    VARIANTS = 5
 
     def __init__(self, grids, *, nonoscillatory: bool = True, tile=(32, 24), eps: float = 1e-15,
-                 periodic=(1, 1, 1)):
+                 periodic=(1, 1, 1), tiles=None):
+        """tile: the default tile; tiles: optional per-grid tile heights
+        (16, 24, or 0 for the default)."""
         o = _lib.default_opts()
         o.nonoscillatory = int(bool(nonoscillatory))
         o.tile_x, o.tile_y = int(tile[0]), int(tile[1])
@@ -182,9 +186,24 @@ class Batch:
             per[3 * i:3 * i + 3] = [int(v) for v in p]
             self.shapes.append((nz, ny, nx))
         self._h = ctypes.c_void_p()
-        check(_lib.lib.mpdata_batch_create(n, dims, per, ctypes.byref(o), ctypes.byref(self._h)),
-              "mpdata_batch_create")
+        if tiles is None:
+            check(_lib.lib.mpdata_batch_create(n, dims, per, ctypes.byref(o), ctypes.byref(self._h)),
+                  "mpdata_batch_create")
+        else:
+            if len(tiles) != n:
+                raise ValueError("tiles needs one tile height per grid")
+            ty = (ctypes.c_int * n)(*[int(v) for v in tiles])
+            check(_lib.lib.mpdata_batch_create_tiles(n, dims, per, ty, ctypes.byref(o),
+                                                     ctypes.byref(self._h)),
+                  "mpdata_batch_create_tiles")
         self._keep = {}
+
+    def grid_variant(self, i) -> int:
+        """Variant (work list) that runs grid i."""
+        v = ctypes.c_int()
+        check(_lib.lib.mpdata_batch_grid_variant(self._h, int(i), ctypes.byref(v)),
+              "mpdata_batch_grid_variant")
+        return v.value
 
     def set_fields(self, i, h, psi, u1, u2, u3) -> None:
         torch = _torch()

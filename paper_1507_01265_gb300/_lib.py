@@ -83,6 +83,8 @@ def _load():
         "mpdata_mass_noalloc": (I, [P, P, ctypes.c_longlong, I, P, P]),
         "mpdata_courant_max": (I, [H, P, P, P, P, P, P]),
         "mpdata_batch_create": (I, [I, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(Opts), ctypes.POINTER(H)]),
+        "mpdata_batch_create_tiles": (I, [I, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(Opts), ctypes.POINTER(H)]),
+        "mpdata_batch_grid_variant": (I, [H, I, ctypes.POINTER(I)]),
         "mpdata_batch_set_fields": (I, [H, I, P, P, P, P, P]),
         "mpdata_batch_work": (I, [H, I, ctypes.POINTER(I), ctypes.POINTER(I)]),
         "mpdata_batch_get_split": (I, [H, I, ctypes.POINTER(I)]),

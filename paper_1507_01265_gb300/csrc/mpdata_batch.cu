@@ -1,8 +1,9 @@
 // Batched persistent launch of many independent grids (C ABI in
 // include/mpdata.h: mpdata_batch_*).
 //
-// Every grid is cut into the same tiles as a single-grid launch.  Tiles of
-// all grids that use the same kernel variant form one work-item list
+// Every grid is cut into the same tiles as a single-grid launch with its
+// tile shape (per grid: 32x24 or 32x16).  Tiles of all grids that use the
+// same kernel variant (kernel, tile shape, lid or not) form one work-item list
 // (grid, tile); a persistent launch of one CTA per SM runs the list, CTA c
 // taking the contiguous items [begin[c], begin[c+1]).  The default split
 // balances the estimated cost (tile area x (nz + 3) planes); callers (the
@@ -28,7 +29,17 @@ using mpdata::Grid;
 
 namespace {
 
-enum Variant { kPairsPeriodic = 0, kPairsLid = 1, kSingle = 2, kNumVariants = 3 };
+enum Variant {
+    kPairs24Periodic = 0,  // two columns per thread, tile 32x24, x and y periodic
+    kPairs24Lid = 1,       // same with a lid on x or y
+    kSingle = 2,           // one column per thread, tile 32x16 (nx % 4 != 0)
+    kPairs16Periodic = 3,  // two columns per thread, tile 32x16
+    kPairs16Lid = 4,
+    kNumVariants = 5
+};
+
+int variant_tile_y(int v) { return (v == kPairs24Periodic || v == kPairs24Lid) ? 24 : 16; }
+bool variant_lid(int v) { return v == kPairs24Lid || v == kPairs16Lid; }
 
 struct Group {
     std::vector<int2> items;  // (grid, tile)
@@ -44,7 +55,6 @@ struct Group {
 struct mpdata_batch {
     int ngrids = 0;
     mpdata_opts opts;
-    int tile_x = 32, tile_y = 24;
     int nsm = 0;
     std::vector<BatchGrid> grids;    // host copy of the descriptors
     std::vector<int> variant;        // per grid
@@ -133,8 +143,8 @@ int enqueue_steps(mpdata_batch *b, int nsteps, cudaStream_t s) {
                 e = mpdata::launch_fused_single_batch(b->opts.nonoscillatory, b->d_grids, G.d_items,
                                                       G.d_begin, G.ncta, parity, s);
             else
-                e = mpdata::launch_fused_pairs_batch(b->tile_x, b->tile_y, b->opts.nonoscillatory,
-                                                     v == kPairsLid, b->d_grids, G.d_items, G.d_begin,
+                e = mpdata::launch_fused_pairs_batch(32, variant_tile_y(v), b->opts.nonoscillatory,
+                                                     variant_lid(v), b->d_grids, G.d_items, G.d_begin,
                                                      G.ncta, parity, s);
             if (e != cudaSuccess) return bcuda(e, "batched kernel launch");
         }
@@ -148,6 +158,11 @@ extern "C" {
 
 int mpdata_batch_create(int ngrids, const int *dims, const int *periodic, const mpdata_opts *opts,
                         mpdata_batch_t **out) {
+    return mpdata_batch_create_tiles(ngrids, dims, periodic, nullptr, opts, out);
+}
+
+int mpdata_batch_create_tiles(int ngrids, const int *dims, const int *periodic, const int *tile_y,
+                              const mpdata_opts *opts, mpdata_batch_t **out) {
     if (!out) return bfail(MPDATA_EINVAL, "out is NULL");
     *out = nullptr;
     if (ngrids < 1 || !dims) return bfail(MPDATA_EINVAL, "need ngrids >= 1 and dims");
@@ -159,15 +174,17 @@ int mpdata_batch_create(int ngrids, const int *dims, const int *periodic, const 
         return bfail(MPDATA_EINVAL, "batches run the FP32 fused step with 2 iterations, the default "
                                     "extrema set and pure precision");
     if (!(o.eps > 0.0)) return bfail(MPDATA_EINVAL, "eps must be > 0");
-    int tx = o.tile_x ? o.tile_x : 32, ty = o.tile_y ? o.tile_y : 24;
-    if (!(tx == 32 && (ty == 16 || ty == 24))) return bfail(MPDATA_EINVAL, "batch tile must be 32x16 or 32x24");
+    const int tx = o.tile_x ? o.tile_x : 32, ty_default = o.tile_y ? o.tile_y : 24;
+    if (!(tx == 32 && (ty_default == 16 || ty_default == 24))) return bfail(MPDATA_EINVAL, "batch tile must be 32x16 or 32x24");
+    if (tile_y)
+        for (int i = 0; i < ngrids; ++i)
+            if (tile_y[i] != 0 && tile_y[i] != 16 && tile_y[i] != 24)
+                return bfail(MPDATA_EINVAL, "tile_y[%d] = %d: must be 0 (the batch default), 16 or 24", i, tile_y[i]);
 
     mpdata_batch *b = new (std::nothrow) mpdata_batch();
     if (!b) return bfail(MPDATA_ENOMEM, "host allocation failed");
     b->ngrids = ngrids;
     b->opts = o;
-    b->tile_x = tx;
-    b->tile_y = ty;
     int dev = 0;
     cudaGetDevice(&dev);
     cudaError_t e = cudaDeviceGetAttribute(&b->nsm, cudaDevAttrMultiProcessorCount, dev);
@@ -192,7 +209,11 @@ int mpdata_batch_create(int ngrids, const int *dims, const int *periodic, const 
             g.g.per[d] = p;
         }
         g.eps = (float)o.eps;
-        int v = mpdata::fused_pairs_supported(g.g, tx, ty) ? ((!g.g.per[0] || !g.g.per[1]) ? kPairsLid : kPairsPeriodic) : kSingle;
+        const int ty = (tile_y && tile_y[i]) ? tile_y[i] : ty_default;
+        const bool lid = !g.g.per[0] || !g.g.per[1];
+        int v = kSingle;
+        if (mpdata::fused_pairs_supported(g.g, tx, ty))
+            v = ty == 24 ? (lid ? kPairs24Lid : kPairs24Periodic) : (lid ? kPairs16Lid : kPairs16Periodic);
         const int gtx = v == kSingle ? 32 : tx, gty = v == kSingle ? 16 : ty;
         g.ntx = (nx + gtx - 1) / gtx;
         const int ntiles = g.ntx * ((ny + gty - 1) / gty);
@@ -233,6 +254,12 @@ int mpdata_batch_set_fields(mpdata_batch_t *b, int grid, const void *h, void *ps
     b->has_fields[grid] = true;
     b->grids_dirty = true;
     drop_graphs(b);
+    return MPDATA_OK;
+}
+
+int mpdata_batch_grid_variant(mpdata_batch_t *b, int grid, int *variant) {
+    if (!b || !variant || grid < 0 || grid >= b->ngrids) return bfail(MPDATA_EINVAL, "bad arguments");
+    *variant = b->variant[grid];
     return MPDATA_OK;
 }
 

@@ -12,7 +12,14 @@ to Algorithm 1 to pick a possibly uneven partition.  The GPU analogue here:
   * for a workload of n tiles the partitioner (mpdata_fpm_partition) returns
     k CTAs with x_right tiles and P - k with x_left, or the balanced split;
   * the speed functions of the available tile shapes are compared and the
-    shape with the shortest predicted step is chosen.
+    shape with the shortest predicted step is chosen;
+  * in a batch of uneven grids each grid may get its own shape
+    (`choose_tiles`): a tile of shape ty costs 32*ty*(nz+3) cell-planes over
+    the per-CTA rate of that shape (measured whole-GPU rate / P); the tiles
+    of one shape form one persistent launch whose time is that of its
+    slowest CTA under the batch's default split, plus a launch.  Starting from the best
+    of the uniform choices and the per-grid cheapest shapes, grids switch
+    shape while the predicted batch time drops.
 
 Usage:  python -m paper_1507_01265_gb300.tune --grid 1024 512 64
 """
@@ -64,7 +71,7 @@ def speed_function(tile=(32, 24), xs=(1, 2, 3, 4, 5, 6, 7, 8), nz=64, steps=6):
         f, t = _device_fields(nx, ny, nz)
         with Batch([(nx, ny, nz, (1, 1, 0))], tile=tile) as b:
             b.set_fields(0, *t)
-            n, ncta = b.work(0)
+            n, ncta = b.work(b.grid_variant(0))
             assert n == P * x and ncta == P
             dt = _time_batch(b, steps)
         speeds.append(x * tx * ty * nz / dt)
@@ -78,6 +85,68 @@ def split_for(n_items, ncta, k, xl, xr):
     if sum(sizes) != n_items:
         raise ValueError("split does not cover the work list")
     return list(np.concatenate([[0], np.cumsum(sizes)]).astype(int))
+
+
+def split_time(costs, nsm):
+    """Time of one persistent launch over items of the given costs with the
+    batch's default split: min(n, nsm) CTAs, boundary c at the item boundary
+    closest to c/ncta of the total cost; the slowest CTA decides."""
+    n = len(costs)
+    if n == 0:
+        return 0.0
+    ncta = min(n, nsm)
+    prefix = np.concatenate([[0.0], np.cumsum(costs)])
+    begin = [0]
+    for c in range(1, ncta):
+        target = prefix[-1] * c / ncta
+        i = int(np.searchsorted(prefix, target, side="left"))
+        if i > 0 and target - prefix[i - 1] < prefix[i] - target:
+            i -= 1
+        begin.append(max(begin[-1], min(i, n)))
+    begin.append(n)
+    return max(prefix[begin[c + 1]] - prefix[begin[c]] for c in range(ncta))
+
+
+def batch_time(dims, tiles, rates, nsm, launch_s=5e-6, tx=32):
+    """Predicted time of one batched step: one persistent launch per tile
+    shape in use (items in batch order, default split), a tile of shape ty
+    costing tx*ty*(nz+3) cell-planes at rates[ty] / nsm per CTA, plus
+    launch_s per launch."""
+    items = {}
+    for (nx, ny, nz), ty in zip(dims, tiles):
+        tile_s = tx * ty * (nz + 3) / (rates[ty] / nsm)
+        items.setdefault(ty, []).extend([tile_s] * (math.ceil(nx / tx) * math.ceil(ny / ty)))
+    return sum(split_time(c, nsm) + launch_s for c in items.values())
+
+
+def choose_tiles(dims, rates, nsm, launch_s=5e-6):
+    """Per-grid tile heights (keys of `rates`, e.g. {24: r24, 16: r16}) for
+    the grids dims = [(nx, ny, nz), ...]: the best of the uniform choices and
+    of every grid taking its own cheapest shape, then single-grid switches
+    (largest predicted gain first) while the predicted batch time drops."""
+    shapes = list(rates)
+
+    def own_cost(nx, ny, nz, ty):
+        return math.ceil(nx / 32) * math.ceil(ny / ty) * 32 * ty * (nz + 3) / rates[ty]
+
+    starts = [[ty] * len(dims) for ty in shapes]
+    starts.append([min(shapes, key=lambda ty: own_cost(nx, ny, nz, ty)) for nx, ny, nz in dims])
+    best = min(starts, key=lambda t: batch_time(dims, t, rates, nsm, launch_s))
+    t_best = batch_time(dims, best, rates, nsm, launch_s)
+    improved = True
+    while improved:
+        improved = False
+        cands = []
+        for i in range(len(dims)):
+            for ty in shapes:
+                if ty != best[i]:
+                    trial = best[:i] + [ty] + best[i + 1:]
+                    cands.append((batch_time(dims, trial, rates, nsm, launch_s), i, ty))
+        if cands:
+            t, i, ty = min(cands)
+            if t < t_best * (1 - 1e-9):
+                best[i], t_best, improved = ty, t, True
+    return best
 
 
 def tune_grid(nx, ny, nz, periodic=(1, 1, 0), steps=10, tiles=((32, 24), (32, 16)), xs_max=10):
@@ -95,8 +164,8 @@ def tune_grid(nx, ny, nz, periodic=(1, 1, 0), steps=10, tiles=((32, 24), (32, 16
         k, xl, xr, t_pred = fpm.partition(ntiles, P, 1.0, xs, ss / (tx * ty * nz))
         with Batch([(nx, ny, nz, periodic)], tile=tile) as b:
             b.set_fields(0, *t)
-            n, ncta = b.work(0 if periodic[0] and periodic[1] else 1)
-            variant = 0 if periodic[0] and periodic[1] else 1
+            variant = b.grid_variant(0)
+            n, ncta = b.work(variant)
             t_bal = _time_batch(b, steps)
             chosen = b.get_split(variant)
             if k > 0:

@@ -117,3 +117,32 @@ def test_bad_tables_are_rejected(fpm):
         fpm.partition(10, 2, 1.0, [2.0, 1.0], [1.0, 1.0])   # sizes not increasing
     with pytest.raises(MpdataError):
         fpm.partition(10, 2, 1.0, [1.0, 2.0], [1.0, -1.0])  # negative speed
+
+
+def test_tile_choice_model():
+    """Per-grid tile heights: the better uniform choice unless a mix lowers
+    the predicted batch time; a mix is chosen where each shape fits its own
+    grids exactly and both launches fill the GPU."""
+    import itertools
+    from paper_1507_01265_gb300 import tune
+    rates = {24: 1e10, 16: 1e10}
+    # ny = 72 fits 32x24 exactly (3 rows; 32x16 needs 5 = 80 rows), ny = 32 fits
+    # 32x16 exactly (2 rows; 32x24 needs 2 = 48 rows)
+    dims = [(1024, 72, 64)] * 20 + [(1024, 32, 64)] * 20
+    t = tune.choose_tiles(dims, rates, nsm=152)
+    got = tune.batch_time(dims, t, rates, 152)
+    clean = tune.batch_time(dims, [24] * 20 + [16] * 20, rates, 152)
+    assert got <= clean < min(tune.batch_time(dims, [ty] * 40, rates, 152) for ty in (24, 16))
+    assert sum(ty == 16 for ty in t[20:]) > 10 and sum(ty == 24 for ty in t[:20]) > 10
+    # a few small grids: a second launch would not fill the GPU, stay uniform
+    small = [(64, 40, 16), (64, 32, 16), (96, 16, 20)]
+    t = tune.choose_tiles(small, rates, nsm=152)
+    assert len(set(t)) == 1
+    # never worse than brute force by more than the greedy's step, never worse than uniform
+    dims = [(256, 40, 32), (128, 56, 16), (512, 16, 64), (64, 88, 24), (320, 72, 48)]
+    t = tune.choose_tiles(dims, {24: 1.1e10, 16: 0.9e10}, nsm=8)
+    got = tune.batch_time(dims, t, {24: 1.1e10, 16: 0.9e10}, 8)
+    brute = min(tune.batch_time(dims, list(a), {24: 1.1e10, 16: 0.9e10}, 8)
+                for a in itertools.product((24, 16), repeat=len(dims)))
+    assert brute <= got <= min(tune.batch_time(dims, [ty] * 5, {24: 1.1e10, 16: 0.9e10}, 8) for ty in (24, 16))
+    assert got <= brute * 1.05

@@ -85,3 +85,37 @@ def test_bad_split_is_rejected(mp):
             b.set_split(0, [1, n])
         with pytest.raises(mp.MpdataError):
             b.step(1)  # fields not set
+
+
+@pytest.mark.parametrize("graph", [False, True])
+def test_per_grid_tiles(mp, graph):
+    """Each grid runs with its own tile height; every result equals the
+    single-grid run with that tile, and the grids land in the documented
+    variants."""
+    import torch
+    tiles = [16, 24, 0, 16, 24, 16, 0]
+    fs = [rand_problem((nz, ny, nx), seed=i + 80, periodic=per) for i, (nx, ny, nz, per) in enumerate(MIX)]
+    ts = _fields(mp, fs)
+    with mp.Batch([(f.nx, f.ny, f.nz, f.periodic) for f in fs], tiles=tiles) as b:
+        want = []
+        for i, (f, ty) in enumerate(zip(fs, tiles)):
+            ty = ty or 24
+            pairs = f.nx % 4 == 0
+            lid = not (f.periodic[0] and f.periodic[1])
+            want.append((0 if ty == 24 else 3) + int(lid) if pairs else 2)
+        assert [b.grid_variant(i) for i in range(len(fs))] == want
+        for i, t in enumerate(ts):
+            b.set_fields(i, *t)
+        b.step(3, graph=graph)
+        torch.cuda.synchronize()
+    for f, t, ty in zip(fs, ts, tiles):
+        tile = (32, ty or 24) if f.nx % 4 == 0 else None
+        assert np.array_equal(t[1].double().cpu().numpy(), run_gpu(f, 3, tile=tile)), (f.name, ty)
+
+
+def test_bad_tile_heights_are_rejected(mp):
+    fs = [rand_problem((4, 8, 32), seed=1), rand_problem((4, 8, 32), seed=2)]
+    with pytest.raises(mp.MpdataError):
+        mp.Batch([(f.nx, f.ny, f.nz, f.periodic) for f in fs], tiles=[16, 8])
+    with pytest.raises(ValueError):
+        mp.Batch([(f.nx, f.ny, f.nz, f.periodic) for f in fs], tiles=[16])
