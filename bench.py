@@ -291,11 +291,10 @@ def run_tracers(args):
 
     every = list(range(len(fs)))
     res["batched"] = time_batch(every)
-    # per-grid tile shapes (two-column grids only; the others run the
-    # one-column kernel whatever the tile): per-shape rates measured on the
-    # two-column grids, then each grid's shape of least predicted cost
+    # per-grid tile shapes: per-shape rates measured on the whole batch, then
+    # each grid's shape from the batch-level model
     from paper_1507_01265_gb300 import tune
-    pairs = [i for i in every if fs[i].nx % 4 == 0]
+    pairs = every
     rates = {}
     for ty in (24, 16):
         ms = time_batch(pairs, tile=(32, ty))
@@ -333,7 +332,7 @@ def run_tracers(args):
             "speedup_vs_per_grid": res["per_grid"] / res["batched"],
             "per_grid_tiles": {"value": cells * nsteps / (res["per_grid_tiles"] * 1e-3) / 1e9,
                                "ms_per_step": res["per_grid_tiles"],
-                               "two_column_grids": len(pairs),
+                               "grids": len(pairs),
                                "tile_y_counts": {str(ty): sum(1 for i in pairs if chosen[i] == ty)
                                                  for ty in (24, 16)},
                                "rates_cell_planes_per_s": {str(k): v for k, v in rates.items()}}}

@@ -78,7 +78,11 @@ typedef struct mpdata_opts {
     int32_t periodic[3];    /* per axis x, y, z: 1 periodic (default), 0 rigid lid */
     int32_t dtype;          /* MPDATA_F32 (default) or MPDATA_F64 */
     int32_t path;           /* MPDATA_PATH_FUSED (default) or MPDATA_PATH_STAGES */
-    int32_t tile_x, tile_y; /* fused-kernel output tile; 0 picks the default */
+    int32_t tile_x, tile_y; /* fused-kernel output tile.  FP32: 32x24 or 32x16 run the
+                               two-column kernel (any nx), 24x24, 24x16, 16x16 the
+                               one-column kernel; FP64: 16x16.  0 x 0 picks the tile
+                               of least predicted step time for the grid on this
+                               device (waves of tiles x measured per-plane time) */
     double eps;             /* > 0, added to every A, B and limiter denominator; default 1e-15 */
     int32_t extrema;        /* MPDATA_EXTREMA_BOTH (default) or _CORRECTED (stage path) */
     int32_t precision;      /* MPDATA_PREC_PURE (default) or _F64_BETA (FP32, stage path) */
@@ -182,11 +186,11 @@ int mpdata_mass_noalloc(const void *h, const void *psi, long long n, int dtype, 
  * contiguous items [begin[c], begin[c+1]).  The default split balances the
  * estimated cost (tile area x (nz + 3)); mpdata_batch_set_split installs any
  * other, e.g. the uneven splits of the speed-function partitioner
- * (Algorithm 1, §4).  Each grid has its own tile shape (32x24 or 32x16).
- * Grids with nx % 4 == 0 use the two-column kernel: variant 0 (tile 32x24,
- * x and y periodic), 1 (32x24, a lid on x or y), 3 (32x16, periodic), 4
- * (32x16, lid); the others the one-column kernel, variant 2 (32x16).  One
- * launch per non-empty variant and step.  FP32, iterations = 2 only.  Each
+ * (Algorithm 1, §4).  Each grid has its own tile shape (32x24 or 32x16)
+ * and runs the two-column kernel: variant 0 (tile 32x24, x and y
+ * periodic), 1 (32x24, a lid on x or y), 3 (32x16, periodic), 4 (32x16,
+ * lid); variant 2 is reserved and stays empty.  One launch per non-empty
+ * variant and step.  FP32, iterations = 2 only.  Each
  * grid's result is bit-identical to mpdata_step on that grid alone with the
  * same tile. */
 typedef struct mpdata_batch mpdata_batch_t;

@@ -146,7 +146,15 @@ int mpdata_create(int nx, int ny, int nz, const mpdata_opts *opts, mpdata_t **ou
     grid.nx = nx; grid.ny = ny; grid.nz = nz;
     for (int d = 0; d < 3; ++d) grid.per[d] = o.periodic[d];
     int tx = o.tile_x, ty = o.tile_y;
-    if (tx == 0 && ty == 0) mpdata::fused_default_tile(o.dtype, grid, &tx, &ty);
+    if (tx == 0 && ty == 0) {
+        int dev = 0, nsm = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+            cudaGetLastError();
+            nsm = 0;  // no device yet: the SM count only tunes the default tile
+        }
+        mpdata::fused_default_tile(o.dtype, grid, nsm, &tx, &ty);
+    }
     if (o.path == MPDATA_PATH_FUSED && o.iterations == 2 && !mpdata::fused_tile_supported(o.dtype, grid, tx, ty))
         return fail(MPDATA_EINVAL, "no fused kernel for tile %d x %d on this grid", tx, ty);
 

@@ -32,7 +32,7 @@ namespace {
 enum Variant {
     kPairs24Periodic = 0,  // two columns per thread, tile 32x24, x and y periodic
     kPairs24Lid = 1,       // same with a lid on x or y
-    kSingle = 2,           // one column per thread, tile 32x16 (nx % 4 != 0)
+    kSingle = 2,           // reserved (no FP32 grid needs the one-column kernel)
     kPairs16Periodic = 3,  // two columns per thread, tile 32x16
     kPairs16Lid = 4,
     kNumVariants = 5
@@ -138,14 +138,9 @@ int enqueue_steps(mpdata_batch *b, int nsteps, cudaStream_t s) {
         for (int v = 0; v < kNumVariants; ++v) {
             Group &G = b->group[v];
             if (G.items.empty()) continue;
-            cudaError_t e;
-            if (v == kSingle)
-                e = mpdata::launch_fused_single_batch(b->opts.nonoscillatory, b->d_grids, G.d_items,
-                                                      G.d_begin, G.ncta, parity, s);
-            else
-                e = mpdata::launch_fused_pairs_batch(32, variant_tile_y(v), b->opts.nonoscillatory,
-                                                     variant_lid(v), b->d_grids, G.d_items, G.d_begin,
-                                                     G.ncta, parity, s);
+            const cudaError_t e = mpdata::launch_fused_pairs_batch(
+                32, variant_tile_y(v), b->opts.nonoscillatory, variant_lid(v), b->d_grids, G.d_items,
+                G.d_begin, G.ncta, parity, s);
             if (e != cudaSuccess) return bcuda(e, "batched kernel launch");
         }
     }
@@ -211,17 +206,14 @@ int mpdata_batch_create_tiles(int ngrids, const int *dims, const int *periodic, 
         g.eps = (float)o.eps;
         const int ty = (tile_y && tile_y[i]) ? tile_y[i] : ty_default;
         const bool lid = !g.g.per[0] || !g.g.per[1];
-        int v = kSingle;
-        if (mpdata::fused_pairs_supported(g.g, tx, ty))
-            v = ty == 24 ? (lid ? kPairs24Lid : kPairs24Periodic) : (lid ? kPairs16Lid : kPairs16Periodic);
-        const int gtx = v == kSingle ? 32 : tx, gty = v == kSingle ? 16 : ty;
-        g.ntx = (nx + gtx - 1) / gtx;
-        const int ntiles = g.ntx * ((ny + gty - 1) / gty);
+        const int v = ty == 24 ? (lid ? kPairs24Lid : kPairs24Periodic) : (lid ? kPairs16Lid : kPairs16Periodic);
+        g.ntx = (nx + tx - 1) / tx;
+        const int ntiles = g.ntx * ((ny + ty - 1) / ty);
         b->variant[i] = v;
         b->bytes[i] = (size_t)nx * ny * nz * sizeof(float);
         for (int tl = 0; tl < ntiles; ++tl) {
             b->group[v].items.push_back(make_int2(i, tl));
-            costs[v].push_back(item_cost(g, gtx, gty));
+            costs[v].push_back(item_cost(g, tx, ty));
         }
         e = cudaMalloc((void **)&g.buf[1], b->bytes[i]);  // scratch partner of psi
         if (e != cudaSuccess) { cudaGetLastError(); mpdata_batch_destroy(b); return bfail(MPDATA_ENOMEM, "scratch allocation for grid %d failed", i); }

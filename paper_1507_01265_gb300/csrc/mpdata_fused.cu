@@ -398,23 +398,6 @@ __global__ void __launch_bounds__(Layout<TX, TY>::NT, 1)
                                    reinterpret_cast<T *>(smem_raw));
 }
 
-// Persistent batched launch (FP32, 32x16 tiles): CTA c runs work items
-// [begin[c], begin[c+1]) of the (grid, tile) list.
-template <bool NONOSC>
-__global__ void __launch_bounds__(Layout<32, 16>::NT, 1)
-    k_fused_single_batch(const BatchGrid *__restrict__ grids, const int2 *__restrict__ items,
-                         const int *__restrict__ begin, int parity) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    float *const sm = reinterpret_cast<float *>(smem_raw);
-    const int lo = begin[blockIdx.x], hi = begin[blockIdx.x + 1];
-    for (int it = lo; it < hi; ++it) {
-        const int2 w = items[it];
-        const TileArgs a = batch_args(grids[w.x], parity);
-        single_tile<float, 32, 16, NONOSC>(a.g, a.eps, a.ntx, a.h, a.psi, a.u1, a.u2, a.u3, a.out,
-                                           w.y, sm);
-    }
-}
-
 template <typename T, int TX, int TY>
 cudaError_t launch_tile(const Grid &g, int nonosc, double eps, const void *h, const void *psi,
                         const void *u1, const void *u2, const void *u3, void *out,
@@ -432,17 +415,6 @@ cudaError_t launch_tile(const Grid &g, int nonosc, double eps, const void *h, co
 
 }  // namespace
 
-cudaError_t launch_fused_single_batch(int nonosc, const BatchGrid *grids, const int2 *items,
-                                      const int *begin, int ncta, int parity, cudaStream_t s) {
-    using L = Layout<32, 16>;
-    const size_t smem = (size_t)L::NPLANES * L::PL * sizeof(float);
-    auto kern = nonosc ? k_fused_single_batch<true> : k_fused_single_batch<false>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    kern<<<ncta, L::NT, smem, s>>>(grids, items, begin, parity);
-    return cudaGetLastError();
-}
-
 static bool single_tile_supported(int dtype, int tx, int ty) {
     if (dtype == MPDATA_F64) return (tx == 16 && ty == 16);
     return (tx == 32 && ty == 16) || (tx == 24 && ty == 24) || (tx == 16 && ty == 16) ||
@@ -454,10 +426,26 @@ bool fused_tile_supported(int dtype, const Grid &g, int tx, int ty) {
     return single_tile_supported(dtype, tx, ty);
 }
 
-void fused_default_tile(int dtype, const Grid &g, int *tx, int *ty) {
-    if (dtype == MPDATA_F64) { *tx = 16; *ty = 16; }
-    else if (fused_pairs_supported(g, 32, 24)) { *tx = 32; *ty = 24; }
-    else { *tx = 32; *ty = 16; }
+void fused_default_tile(int dtype, const Grid &g, int nsm, int *tx, int *ty) {
+    if (dtype == MPDATA_F64) { *tx = 16; *ty = 16; return; }
+    // FP32: the tile of least predicted step time, waves x per-plane time of
+    // one CTA, waves = ceil(tiles / SMs) (one CTA per SM).  Per-plane times
+    // measured on GB300 (us, nz 33..63): a small grid (one wave) wants the
+    // smallest, fastest plane; a large one the most cells per plane-time.
+    struct Cand { int tx, ty; double us_aligned, us_any; };
+    static const Cand cands[] = {
+        {32, 24, 1.91, 2.66},  // two-column kernel (16-byte loads if nx % 4 == 0)
+        {32, 16, 1.55, 2.04},
+        {24, 16, 1.86, 1.86},  // one-column kernel
+        {16, 16, 1.51, 1.51},
+    };
+    const int sms = nsm > 0 ? nsm : 1 << 30;  // unknown device: every grid is one wave
+    double best = 0.0;
+    for (const Cand &c : cands) {
+        const long long tiles = (long long)((g.nx + c.tx - 1) / c.tx) * ((g.ny + c.ty - 1) / c.ty);
+        const double t = (double)((tiles + sms - 1) / sms) * (g.nx % 4 == 0 ? c.us_aligned : c.us_any);
+        if (best == 0.0 || t < best * 0.98) { best = t; *tx = c.tx; *ty = c.ty; }
+    }
 }
 
 cudaError_t launch_fused_step(int dtype, const Grid &g, int nonosc, double eps, int tx, int ty,

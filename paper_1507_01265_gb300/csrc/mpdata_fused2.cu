@@ -9,8 +9,12 @@
 //     with packed f32x2 add/mul/fma, so per-thread overhead (addressing,
 //     predicates, loop control) is paid once per two cells and shared-memory
 //     neighbours of the pair come in one 64-bit load;
-//   * inputs stream in as 16-byte cp.async chunks (this kernel requires nx to
-//     be a multiple of 4 so that chunks never straddle a wrap or a lid);
+//   * inputs stream in as 16-byte cp.async chunks when nx is a multiple of 4
+//     (chunks then never straddle a wrap or a lid and rows stay 16-byte
+//     aligned); for any other nx the same chunks move as four 4-byte copies,
+//     element by element where a chunk crosses the x wrap or lid.  Columns
+//     past nx are ghosts: wrapped copies on a periodic axis, zero-filled faces
+//     and clamped cell values behind a lid, never stored;
 //   * when x and y are both periodic (LID = false) every neighbour offset is
 //     a compile-time constant; with a lid on x or y (LID = true) the neighbour
 //     reads of cell fields are clamped (zero-gradient ghosts) and the lid
@@ -145,6 +149,11 @@ __device__ __forceinline__ void cp16(unsigned dst, const float *src, bool zero) 
                  "r"(zero ? 0 : 16)
                  : "memory");
 }
+__device__ __forceinline__ void cp4(unsigned dst, const float *src, bool zero) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(dst), "l"(src),
+                 "r"(zero ? 0 : 4)
+                 : "memory");
+}
 
 // Shared-memory access with explicit 32-bit addresses: one per-thread base
 // plus per-iteration slot bases; every field, plane and neighbour offset is a
@@ -168,7 +177,9 @@ __device__ __forceinline__ void stp(unsigned b, F2 v) {
 
 // One tile (tile index `tile` of grid a.g, tiles numbered row-major with
 // a.ntx tiles per row) marched through all z planes by the whole CTA.
-template <int TX, int TY, bool NONOSC, bool LID>
+// AL: 1 = nx % 4 == 0 (16-byte loads, 8-byte stores), 0 = any nx (4-byte
+// loads, per-column stores), 2 = decided per tile from nx.
+template <int TX, int TY, bool NONOSC, bool LID, int AL>
 __device__ __forceinline__ void pairs_tile(const TileArgs &a, int tile, float *sm) {
     using L = Lay2<TX, TY>;
     const Grid &g = a.g;
@@ -206,6 +217,9 @@ __device__ __forceinline__ void pairs_tile(const TileArgs &a, int tile, float *s
     const bool clampR = LID && !perx && gx + 1 == nx - 1;
     const int dD = (LID && !pery && gy == 0) ? 0 : -RB;       // clamped row below (bytes)
     const int dU = (LID && !pery && gy == ny - 1) ? 0 : RB;   // clamped row above
+    // with odd nx the last column is the .x of a pair: its right ghost clamps to itself
+    const bool clampRx = LID && AL != 1 && !perx && gx == nx - 1;
+    const bool a16 = AL == 1 || (AL == 2 && (nx & 3) == 0);
     const bool xlid0 = LID && !perx && (gx <= 0 || gx >= nx);
     const bool xlid1 = LID && !perx && (gx + 1 <= 0 || gx + 1 >= nx);
     const bool ylid = LID && !pery && (gy <= 0 || gy >= ny);
@@ -220,25 +234,43 @@ __device__ __forceinline__ void pairs_tile(const TileArgs &a, int tile, float *s
     // pairs shifted by one column, (col-1, col) and (col+1, col+2): cell
     // fields clamp on an x-lid, face fields do not
     auto lshC = [&](unsigned b, F2 own) { float a = lds<-4>(b); return make_float2(clampL ? own.x : a, own.x); };
-    auto rshC = [&](unsigned b, F2 own) { float a = lds<8>(b); return make_float2(own.y, clampR ? own.y : a); };
+    auto rshC = [&](unsigned b, F2 own) {
+        float a = lds<8>(b);
+        return make_float2(clampRx ? own.x : own.y, clampR ? own.y : a);
+    };
     auto lshF = [&](unsigned b, F2 own) { return make_float2(lds<-4>(b), own.x); };
     auto rshF = [&](unsigned b, F2 own) { return make_float2(own.y, lds<8>(b)); };
     auto lid2 = [&](F2 v, bool a, bool c) { return make_float2(a ? 0.f : v.x, c ? 0.f : v.y); };
 
-    // ---- this thread's 16-byte load chunk of the radius-3 plane ----
+    // ---- this thread's load chunk (4 columns of one row) of the radius-3 plane ----
     const bool has_chunk = t < L::NCH;
-    int ld_off = 0;
-    bool z_all = false, z_u2 = false, patch_u1 = false;
+    int ld_off = 0, lx = 0;
+    bool z_all = false, z_u2 = false, z_row = false, y_face0 = false, patch_u1 = false, contig = true;
     unsigned ld_dst = 0;
     if (has_chunk) {
         const int ey = t / L::CPR, cc = t % L::CPR;
-        const int lx = x0 - 4 + 4 * cc, ly = y0 - 3 + ey;
+        lx = x0 - 4 + 4 * cc;
+        const int ly = y0 - 3 + ey;
         int cx, cy;
         bool outx = false, outy = false;
-        if (perx) cx = wrap(lx, nx); else { outx = lx < 0 || lx >= nx; cx = outx ? 0 : lx; }
-        if (pery) cy = wrap(ly, ny); else { outy = ly < 0 || ly >= ny; cy = outy ? 0 : ly; }
-        z_all = outx || outy;                    // lid ghost: never read as a cell value
-        z_u2 = z_all || (!pery && ly == 0);      // y-lid face 0
+        if constexpr (AL == 1) {
+            if (perx) cx = wrap(lx, nx); else { outx = lx < 0 || lx >= nx; cx = outx ? 0 : lx; }
+            if (pery) cy = wrap(ly, ny); else { outy = ly < 0 || ly >= ny; cy = outy ? 0 : ly; }
+            z_all = outx || outy;                // lid ghost: never read as a cell value
+            z_u2 = z_all || (!pery && ly == 0);  // y-lid face 0
+        } else {
+            if (pery) cy = wrap(ly, ny); else { outy = ly < 0 || ly >= ny; cy = outy ? 0 : ly; }
+            if (a16) {
+                if (perx) cx = wrap(lx, nx); else { outx = lx < 0 || lx >= nx; cx = outx ? 0 : lx; }
+            } else {
+                contig = lx >= 0 && lx + 3 < nx;  // the 4 columns are consecutive in memory
+                cx = contig ? lx : 0;
+            }
+            z_row = outy;                         // y-lid ghost row
+            z_all = outx || outy;
+            y_face0 = !pery && ly == 0;
+            z_u2 = z_all || y_face0;
+        }
         patch_u1 = LID && !perx && lx == 0;      // x-lid face 0 is this chunk's first element
         ld_off = cy * nx + cx;
         ld_dst = sm_base + (unsigned)(ey * EX + 4 * cc) * 4u;
@@ -248,11 +280,31 @@ __device__ __forceinline__ void pairs_tile(const TileArgs &a, int tile, float *s
             const long long pc = (long long)(perz ? wrap(p, nz) : min(max(p, 0), nz - 1)) * nxy + ld_off;
             const bool zz = !perz && (p <= 0 || p >= nz);  // z-lid face
             const unsigned d = ld_dst + (unsigned)(slot5(p) * PB);
-            cp16(d, psi + pc, z_all);
-            cp16(d + FB, u1 + pc, z_all);
-            cp16(d + 2 * FB, u2 + pc, z_u2);
-            cp16(d + 3 * FB, u3 + pc, z_all || zz);
-            cp16(d + 4 * FB, h + pc, z_all);
+            if (a16) {
+                cp16(d, psi + pc, z_all);
+                cp16(d + FB, u1 + pc, z_all);
+                cp16(d + 2 * FB, u2 + pc, z_u2);
+                cp16(d + 3 * FB, u3 + pc, z_all || zz);
+                cp16(d + 4 * FB, h + pc, z_all);
+            } else {
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    long long o = pc + e;
+                    bool ze = z_row;
+                    if (!contig) {  // crosses the x wrap or an x lid: map this column
+                        const int x = lx + e;
+                        int c;
+                        if (perx) c = wrap(x, nx); else { ze = ze || x < 0 || x >= nx; c = (x < 0 || x >= nx) ? 0 : x; }
+                        o = pc + c;
+                    }
+                    const unsigned de = d + 4u * e;
+                    cp4(de, psi + o, ze);
+                    cp4(de + FB, u1 + o, ze);
+                    cp4(de + 2 * FB, u2 + o, ze || y_face0);
+                    cp4(de + 3 * FB, u3 + o, ze || zz);
+                    cp4(de + 4 * FB, h + o, ze);
+                }
+            }
         }
         asm volatile("cp.async.commit_group;\n" ::: "memory");
     };
@@ -404,7 +456,16 @@ __device__ __forceinline__ void pairs_tile(const TileArgs &a, int tile, float *s
                 }
                 gz = flux(vm3, p1a, p1b);
             }
-            if (q3ok && store) st2(outp + (long long)q3 * nxy, sub(p1a, mul(add(dacc, gz), rcp(h_prev))));
+            if (q3ok && store) {
+                const F2 v = sub(p1a, mul(add(dacc, gz), rcp(h_prev)));
+                float *const o = outp + (long long)q3 * nxy;
+                if (a16) {
+                    st2(o, v);
+                } else {  // any nx: the pair may end past nx and need not be 8-byte aligned
+                    o[0] = v.x;
+                    if (gx + 1 < nx) o[1] = v.y;
+                }
+            }
             dacc = sub(Z, gz);
         }
         // (a1) donor pass at plane p (psi^n at p-1, p, p+1)
@@ -438,10 +499,10 @@ __device__ __forceinline__ void pairs_tile(const TileArgs &a, int tile, float *s
     __syncthreads();  // shared memory is reused by the next tile of a persistent CTA
 }
 
-template <int TX, int TY, bool NONOSC, bool LID>
+template <int TX, int TY, bool NONOSC, bool LID, int AL>
 __global__ void __launch_bounds__(Lay2<TX, TY>::NT, 1) k_fused_pairs(TileArgs a) {
     extern __shared__ __align__(16) float sm[];
-    pairs_tile<TX, TY, NONOSC, LID>(a, blockIdx.x, sm);
+    pairs_tile<TX, TY, NONOSC, LID, AL>(a, blockIdx.x, sm);
 }
 
 // Persistent batched launch: CTA c runs work items [begin[c], begin[c+1]) of
@@ -455,7 +516,7 @@ __global__ void __launch_bounds__(Lay2<TX, TY>::NT, 1)
     const int lo = begin[blockIdx.x], hi = begin[blockIdx.x + 1];
     for (int it = lo; it < hi; ++it) {
         const int2 w = items[it];
-        pairs_tile<TX, TY, NONOSC, LID>(batch_args(grids[w.x], parity), w.y, sm);
+        pairs_tile<TX, TY, NONOSC, LID, 2>(batch_args(grids[w.x], parity), w.y, sm);
     }
 }
 
@@ -466,8 +527,14 @@ cudaError_t launch_pairs(const Grid &g, int nonosc, double eps, const void *h, c
     const size_t smem = (size_t)L::NPLANES * L::PL * sizeof(float);
     const int ntx = (g.nx + TX - 1) / TX, nty = (g.ny + TY - 1) / TY;
     const bool lid = !g.per[0] || !g.per[1];
-    auto kern = nonosc ? (lid ? k_fused_pairs<TX, TY, true, true> : k_fused_pairs<TX, TY, true, false>)
-                       : (lid ? k_fused_pairs<TX, TY, false, true> : k_fused_pairs<TX, TY, false, false>);
+    const bool a16 = g.nx % 4 == 0;
+    void (*kern)(TileArgs);
+    if (a16)
+        kern = nonosc ? (lid ? k_fused_pairs<TX, TY, true, true, 1> : k_fused_pairs<TX, TY, true, false, 1>)
+                      : (lid ? k_fused_pairs<TX, TY, false, true, 1> : k_fused_pairs<TX, TY, false, false, 1>);
+    else
+        kern = nonosc ? (lid ? k_fused_pairs<TX, TY, true, true, 0> : k_fused_pairs<TX, TY, true, false, 0>)
+                      : (lid ? k_fused_pairs<TX, TY, false, true, 0> : k_fused_pairs<TX, TY, false, false, 0>);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     TileArgs a;
@@ -496,14 +563,13 @@ cudaError_t launch_pairs_batch(int nonosc, int lid, const BatchGrid *grids, cons
 }  // namespace
 
 bool fused_pairs_supported(const Grid &g, int tx, int ty) {
-    if (g.nx % 4 != 0) return false;
+    (void)g;  // any nx: 16-byte loads when nx % 4 == 0, 4-byte loads otherwise
     return tx == 32 && (ty == 16 || ty == 24);
 }
 
 cudaError_t launch_fused_pairs(const Grid &g, int nonosc, double eps, int tx, int ty, const void *h,
                                const void *psi, const void *u1, const void *u2, const void *u3,
                                void *out, cudaStream_t s) {
-    if (g.nx % 4 != 0) return cudaErrorInvalidValue;
     if (tx == 32 && ty == 16) return launch_pairs<32, 16>(g, nonosc, eps, h, psi, u1, u2, u3, out, s);
     if (tx == 32 && ty == 24) return launch_pairs<32, 24>(g, nonosc, eps, h, psi, u1, u2, u3, out, s);
     return cudaErrorInvalidValue;

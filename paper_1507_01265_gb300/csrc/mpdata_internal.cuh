@@ -83,14 +83,13 @@ cudaError_t launch_fused_step(int dtype, const Grid &g, int nonosc, double eps, 
                               int tile_y, const void *h, const void *psi, const void *u1,
                               const void *u2, const void *u3, void *out, cudaStream_t s);
 bool fused_tile_supported(int dtype, const Grid &g, int tile_x, int tile_y);
-void fused_default_tile(int dtype, const Grid &g, int *tile_x, int *tile_y);
+// nsm: SMs of the device (small grids with nx % 4 != 0 get one-column tiles).
+void fused_default_tile(int dtype, const Grid &g, int nsm, int *tile_x, int *tile_y);
 bool fused_pairs_supported(const Grid &g, int tile_x, int tile_y);
 // Persistent batched launches (ncta CTAs; CTA c runs items [begin[c], begin[c+1])).
 cudaError_t launch_fused_pairs_batch(int tile_x, int tile_y, int nonosc, int lid,
                                      const BatchGrid *grids, const int2 *items, const int *begin,
                                      int ncta, int parity, cudaStream_t s);
-cudaError_t launch_fused_single_batch(int nonosc, const BatchGrid *grids, const int2 *items,
-                                      const int *begin, int ncta, int parity, cudaStream_t s);
 cudaError_t launch_fused_pairs(const Grid &g, int nonosc, double eps, int tile_x, int tile_y,
                                const void *h, const void *psi, const void *u1, const void *u2,
                                const void *u3, void *out, cudaStream_t s);

@@ -47,7 +47,9 @@ int sfail(int code, const char *fmt, ...) {
     return mpdata::set_error(code, buf);
 }
 
-enum Variant { kPairsPeriodic = 0, kPairsLid = 1, kSingle = 2, kNumVariants = 3 };
+// Kernel variants of a tick: the two-column kernel with x and y periodic, or
+// with a lid on x or y (every FP32 grid runs the two-column kernel).
+enum Variant { kPairsPeriodic = 0, kPairsLid = 1, kNumVariants = 2 };
 
 struct Request {
     uint64_t ticket = 0;
@@ -57,7 +59,7 @@ struct Request {
     std::atomic<bool> cancel{false};
     size_t field_bytes = 0, bytes = 0;
     int remaining = 0;
-    int variant = kSingle, ntiles = 0;
+    int variant = kPairsPeriodic, ntiles = 0;
     BatchGrid bg;  // buf[0] holds the current state, buf[1] its partner
     float *dev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     cudaEvent_t done_ev = nullptr;
@@ -188,13 +190,13 @@ cudaError_t run_tick(mpdata_server *s, const std::vector<Request *> &act, int ch
     const int na = (int)act.size();
     T.h_grids.resize(na);
     T.h_items.clear();
-    int voff[kNumVariants] = {0, 0, 0};
+    int voff[kNumVariants] = {0, 0};
     std::vector<double> cost[kNumVariants];
     std::vector<int2> items[kNumVariants];
     for (int a = 0; a < na; ++a) {
         Request *r = act[a];
         T.h_grids[a] = r->bg;
-        const int ty = r->variant == kSingle ? 16 : s->o.tile_y;
+        const int ty = s->o.tile_y;
         for (int t = 0; t < r->ntiles; ++t) {
             items[r->variant].push_back(make_int2(a, t));
             cost[r->variant].push_back(32.0 * ty * (r->bg.g.nz + 3));
@@ -229,11 +231,7 @@ cudaError_t run_tick(mpdata_server *s, const std::vector<Request *> &act, int ch
         for (int v = 0; v < kNumVariants && e == cudaSuccess; ++v) {
             if (!ncta[v]) continue;
             const int *begin = T.d_begin + voff[v];
-            if (v == kSingle)
-                e = mpdata::launch_fused_single_batch(s->o.nonoscillatory, T.d_grids, T.d_items, begin,
-                                                      ncta[v], parity, s->stream);
-            else
-                e = mpdata::launch_fused_pairs_batch(32, s->o.tile_y, s->o.nonoscillatory, v == kPairsLid,
+            e = mpdata::launch_fused_pairs_batch(32, s->o.tile_y, s->o.nonoscillatory, v == kPairsLid,
                                                      T.d_grids, T.d_items, begin, ncta[v], parity, s->stream);
         }
     }
@@ -446,8 +444,8 @@ int mpdata_submit(mpdata_server_t *s, const mpdata_request *req, uint64_t *ticke
     g.g.nx = nx; g.g.ny = ny; g.g.nz = nz;
     for (int d = 0; d < 3; ++d) g.g.per[d] = req->periodic[d];
     g.eps = (float)s->o.eps;
-    r->variant = mpdata::fused_pairs_supported(g.g, 32, s->o.tile_y) ? ((!g.g.per[0] || !g.g.per[1]) ? kPairsLid : kPairsPeriodic) : kSingle;
-    const int tx = 32, ty = r->variant == kSingle ? 16 : s->o.tile_y;
+    r->variant = (!g.g.per[0] || !g.g.per[1]) ? kPairsLid : kPairsPeriodic;
+    const int tx = 32, ty = s->o.tile_y;
     g.ntx = (nx + tx - 1) / tx;
     r->ntiles = g.ntx * ((ny + ty - 1) / ty);
     std::lock_guard<std::mutex> lk(s->mu);

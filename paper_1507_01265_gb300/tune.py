@@ -21,7 +21,12 @@ to Algorithm 1 to pick a possibly uneven partition.  The GPU analogue here:
     of the uniform choices and the per-grid cheapest shapes, grids switch
     shape while the predicted batch time drops.
 
+  * `tile_times` measures the step time of single-grid launches per tile
+    shape (the data behind the library's default-tile model: waves of tiles
+    x per-plane time of one CTA).
+
 Usage:  python -m paper_1507_01265_gb300.tune --grid 1024 512 64
+        python -m paper_1507_01265_gb300.tune --tile-probe 40
 """
 from __future__ import annotations
 
@@ -185,12 +190,69 @@ def tune_grid(nx, ny, nz, periodic=(1, 1, 0), steps=10, tiles=((32, 24), (32, 16
     return report
 
 
+TILES = ((32, 24), (32, 16), (24, 24), (24, 16), (16, 16))
+
+
+def probe_grids(count=40, seed=1511):
+    """Grid sizes of the serving workload's request templates: nx, ny, nz
+    log-uniform in [32, 512] x [32, 256] x [32, 64] (drawn as in bench.py)."""
+    import gen.fields as F
+    st = F.Stream(seed)
+    out = []
+    for _ in range(count):
+        nx = st.log_uniform_int(32, 512)
+        ny = st.log_uniform_int(32, 256)
+        nz = st.log_uniform_int(32, 64)
+        st.scalar(0.1, 0.5)
+        out.append((nx, ny, nz))
+    return out
+
+
+def tile_times(grids, tiles=TILES, steps=20):
+    """Microseconds per step of one mpdata_step launch per tile shape, for
+    each (nx, ny, nz) (x/y periodic, lid z), plus the default tile the
+    library picks."""
+    import torch
+    from . import Solver
+    rows = []
+    for nx, ny, nz in grids:
+        f, t = _device_fields(nx, ny, nz)
+        us = {}
+        for tile in tiles:
+            with Solver(nx, ny, nz, periodic=(1, 1, 0), tile=tile) as s:
+                p = t[1].clone()
+                s.step(t[0], p, t[2], t[3], t[4], 2)
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                s.step(t[0], p, t[2], t[3], t[4], steps)
+                e1.record()
+                torch.cuda.synchronize()
+                us["%dx%d" % tile] = e0.elapsed_time(e1) / steps * 1e3
+        with Solver(nx, ny, nz, periodic=(1, 1, 0)) as s:
+            default = "%dx%d" % s.tile
+        rows.append({"grid": [nx, ny, nz], "us": us, "best": min(us, key=us.get), "default": default})
+        del t
+    return rows
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--grid", type=int, nargs=3, default=[1024, 512, 64])
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--xs-max", type=int, default=8)
+    ap.add_argument("--tile-probe", type=int, default=0, metavar="N",
+                    help="time every tile shape on N serving-size grids instead")
     a = ap.parse_args()
+    if a.tile_probe:
+        rows = tile_times(probe_grids(a.tile_probe))
+        for r in rows:
+            print(json.dumps(r))
+        best = sum(min(r["us"].values()) for r in rows)
+        dflt = sum(r["us"][r["default"]] for r in rows)
+        print(json.dumps({"sum_us_best": best, "sum_us_default": dflt,
+                          "sum_us_by_tile": {k: sum(r["us"][k] for r in rows) for k in rows[0]["us"]}}))
+        return
     rep = tune_grid(*a.grid, steps=a.steps, xs_max=a.xs_max)
     print(json.dumps(rep))
 

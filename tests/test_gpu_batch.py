@@ -20,7 +20,7 @@ def mp():
     return mp
 
 
-MIX = [  # (nx, ny, nz, periodic): two-column periodic, two-column lid, one-column
+MIX = [  # (nx, ny, nz, periodic): x/y periodic or lids; nx % 4 == 0 (16-byte loads) or not
     (64, 40, 12, (1, 1, 1)), (36, 50, 7, (1, 1, 0)), (40, 30, 10, (0, 1, 1)),
     (37, 23, 11, (1, 1, 1)), (9, 40, 7, (0, 1, 0)), (96, 24, 4, (1, 0, 1)), (4, 3, 2, (1, 1, 1)),
 ]
@@ -49,7 +49,7 @@ def test_batch_equals_alone(mp, nsteps, graph, nonosc):
         b.step(nsteps, graph=graph)  # a second run reuses the cached graph
         torch.cuda.synchronize()
     for f, t in zip(fs, ts):
-        alone = run_gpu(f, 2 * nsteps, nonosc=nonosc)
+        alone = run_gpu(f, 2 * nsteps, nonosc=nonosc, tile=(32, 24))  # the batch tile
         assert np.array_equal(t[1].double().cpu().numpy(), alone), f.name
 
 
@@ -99,18 +99,15 @@ def test_per_grid_tiles(mp, graph):
     with mp.Batch([(f.nx, f.ny, f.nz, f.periodic) for f in fs], tiles=tiles) as b:
         want = []
         for i, (f, ty) in enumerate(zip(fs, tiles)):
-            ty = ty or 24
-            pairs = f.nx % 4 == 0
             lid = not (f.periodic[0] and f.periodic[1])
-            want.append((0 if ty == 24 else 3) + int(lid) if pairs else 2)
+            want.append((0 if (ty or 24) == 24 else 3) + int(lid))
         assert [b.grid_variant(i) for i in range(len(fs))] == want
         for i, t in enumerate(ts):
             b.set_fields(i, *t)
         b.step(3, graph=graph)
         torch.cuda.synchronize()
     for f, t, ty in zip(fs, ts, tiles):
-        tile = (32, ty or 24) if f.nx % 4 == 0 else None
-        assert np.array_equal(t[1].double().cpu().numpy(), run_gpu(f, 3, tile=tile)), (f.name, ty)
+        assert np.array_equal(t[1].double().cpu().numpy(), run_gpu(f, 3, tile=(32, ty or 24))), (f.name, ty)
 
 
 def test_bad_tile_heights_are_rejected(mp):

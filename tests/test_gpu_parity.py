@@ -52,7 +52,7 @@ EDGE = [
     (37, 23, 11, (1, 1, 1)), (5, 3, 2, (1, 1, 1)), (1, 1, 1, (1, 1, 1)), (1, 1, 1, (0, 0, 0)),
     (9, 40, 7, (0, 1, 0)), (70, 5, 3, (1, 0, 0)), (33, 17, 20, (1, 1, 0)), (64, 32, 16, (0, 0, 0)),
     (32, 16, 4, (1, 1, 1)), (31, 15, 6, (0, 1, 1)), (65, 33, 3, (1, 0, 1)), (2, 70, 2, (0, 0, 1)),
-    # nx % 4 == 0: the two-columns-per-thread kernel (periodic and lid variants)
+    # nx % 4 == 0: 16-byte loads in the two-column kernel (others: 4-byte loads)
     (40, 30, 10, (0, 1, 1)), (36, 50, 5, (1, 0, 1)), (8, 8, 8, (0, 0, 0)), (4, 3, 2, (1, 1, 1)),
     (100, 26, 9, (1, 1, 0)), (64, 49, 6, (1, 0, 0)), (96, 24, 4, (1, 1, 1)), (4, 1, 1, (0, 1, 0)),
 ]
@@ -71,8 +71,6 @@ def test_edge_shapes_f64(nx, ny, nz, per, nonosc):
 @pytest.mark.parametrize("nx,ny,nz,per", EDGE)
 @pytest.mark.parametrize("tile", [None, (24, 24), (16, 16), (32, 16), (32, 24)])
 def test_edge_shapes_f32(nx, ny, nz, per, tile):
-    if tile == (32, 24) and nx % 4:
-        pytest.skip("the 32x24 tile exists only for the two-column kernel (nx % 4 == 0)")
     f = rand_problem((nz, ny, nx), seed=nx * 17 + ny * 5 + nz, periodic=per)
     want = run_oracle(f, 3)
     got = run_gpu(f, 3, tile=tile)
@@ -80,8 +78,9 @@ def test_edge_shapes_f32(nx, ny, nz, per, tile):
 
 
 @pytest.mark.parametrize("per", [(1, 1, 0), (0, 0, 1)])
-def test_pair_kernel_matches_single_column_kernel(per):
-    f = rand_problem((12, 40, 64), seed=21, periodic=per)
+@pytest.mark.parametrize("nx", [64, 63, 66, 33])
+def test_pair_kernel_matches_single_column_kernel(per, nx):
+    f = rand_problem((12, 40, nx), seed=21, periodic=per)
     a = run_gpu(f, 6, tile=(32, 24))   # two columns per thread
     b = run_gpu(f, 6, tile=(24, 24))   # one column per thread
     assert rel_err(a, b) <= 1e-6

@@ -60,7 +60,7 @@ def test_results_equal_alone_in_the_mix(mp):
         st = srv.stats()
         assert st["completed"] == len(fs) and st["resident"] == 0 and st["admitted_bytes"] == 0
     for f, o in zip(fs, outs):
-        assert np.array_equal(o.astype(np.float64), run_gpu(f, f.nsteps)), f.name
+        assert np.array_equal(o.astype(np.float64), run_gpu(f, f.nsteps, tile=(32, 24))), f.name
 
 
 def test_budget_refusal_timeout_cancel(mp):
@@ -84,7 +84,7 @@ def test_budget_refusal_timeout_cancel(mp):
         b = f.psi.copy()
         tb = srv.submit(f.h, b, f.u1, f.u2, f.u3, 3, periodic=f.periodic)
         srv.wait(tb, timeout_ms=60000)
-        assert np.array_equal(b.astype(np.float64), run_gpu(f, 3))
+        assert np.array_equal(b.astype(np.float64), run_gpu(f, 3, tile=(32, 24)))
         with pytest.raises(mp.MpdataError) as e:
             srv.poll(999999)
         assert e.value.code == mp._lib.MPDATA_ENOENT
@@ -108,4 +108,4 @@ def test_injected_allocation_failure(mp):
                 codes.append(e.code)
     assert codes == [0, mp._lib.MPDATA_ENOMEM, 0, mp._lib.MPDATA_ENOMEM]
     for i in (0, 2):
-        assert np.array_equal(outs[i].astype(np.float64), run_gpu(fs[i], fs[i].nsteps))
+        assert np.array_equal(outs[i].astype(np.float64), run_gpu(fs[i], fs[i].nsteps, tile=(32, 24)))
