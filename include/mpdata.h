@@ -93,7 +93,10 @@ typedef struct mpdata_handle mpdata_t;
 /* Fill *opts with the defaults listed above. */
 void mpdata_opts_default(mpdata_opts *opts);
 
-/* Create a solver for an nx x ny x nz grid on the current CUDA device.
+/* Create a solver for an nx x ny x nz grid on the current CUDA device: the
+ * MPDATA step of §5.2, run (path FUSED) with all its stages in one kernel
+ * pass over the grid, the GPU form of the paper's fused block-wise
+ * execution (§5.3), or (path STAGES) one kernel per stage.
  * Limits: each dimension >= 1, ny and nz <= 65535, nx * ny < 2^31 (one
  * z-plane), nx * ny * nz < 2^40 (beyond 2^31 cells the grid is addressed
  * with 64-bit plane offsets; device memory is the practical limit: 6 fields
@@ -114,7 +117,9 @@ int mpdata_destroy(mpdata_t *handle);
  * stage path.  Errors: EINVAL (NULL argument). */
 int mpdata_get_tile(const mpdata_t *handle, int *tile_x, int *tile_y);
 
-/* Advance psi by nsteps MPDATA steps in place (async on `stream`).
+/* Advance psi by nsteps MPDATA steps in place (async on `stream`): each
+ * step reads the five fields and writes psi (§5.2); a run is a loop of such
+ * steps (§6 times 40 of them).
  * h, u1, u2, u3, psi: device pointers to nx*ny*nz elements of the handle's
  * dtype; psi is read and overwritten, the others only read.  Step s reads
  * one buffer and writes the other of the pair (psi, handle scratch); when
@@ -124,14 +129,15 @@ int mpdata_get_tile(const mpdata_t *handle, int *tile_x, int *tile_y);
 int mpdata_step(mpdata_t *handle, const void *h, void *psi, const void *u1, const void *u2,
                 const void *u3, int nsteps, void *stream);
 
-/* Same as mpdata_step on HOST arrays: copies h, psi, u1, u2, u3 to device
+/* Same as mpdata_step (§5.2) on HOST arrays: copies h, psi, u1, u2, u3 to device
  * buffers owned by the handle (allocated on first use), runs nsteps steps
  * and copies psi back, then waits for the stream.  Returns when psi holds
  * the result.  Errors: EINVAL, ENOMEM, ECUDA. */
 int mpdata_solve_host(mpdata_t *handle, const void *h, void *psi, const void *u1,
                       const void *u2, const void *u3, int nsteps, void *stream);
 
-/* Diagnostics (async): out3[0] = sum of h*psi over all cells, out3[1] =
+/* Diagnostics (async; the paper defines none: sum h*psi is the quantity the
+ * flux form of the §5.2 scheme conserves): out3[0] = sum of h*psi over all cells, out3[1] =
  * min psi, out3[2] = max psi, written as three doubles to the DEVICE
  * pointer out3.  The sum is taken in FP64 with a fixed reduction tree (no
  * atomics on values), so it is bit-reproducible run to run.
@@ -226,6 +232,8 @@ int mpdata_batch_step(mpdata_batch_t *batch, int nsteps, int use_graph, void *st
 int mpdata_batch_destroy(mpdata_batch_t *batch);
 
 /* ---- serving: continuous batching of advection solves ----
+ * (No counterpart in the paper: a front end that runs many independent
+ * solves of the §5.2 step on one GPU.)
  *
  * A server owns a scheduler thread and a CUDA stream on the device current at
  * creation.  Requests (host fields, FP32) are admitted first-in first-out
@@ -236,7 +244,7 @@ int mpdata_batch_destroy(mpdata_batch_t *batch);
  * arrive while others run join at the next tick and share the GPU.  A
  * finished request's psi is copied back into its host buffer, then its
  * memory and budget are released.  Each result is bit-identical to
- * mpdata_step on that grid alone.  Host buffers must stay valid until the
+ * mpdata_step on that grid alone with tile 32 x tile_y.  Host buffers must stay valid until the
  * request finishes; pinned memory keeps the scheduler from blocking on
  * copies.  All entry points are thread-safe. */
 #define MPDATA_REQ_QUEUED 0    /* waiting for budget or a slot */
