@@ -78,7 +78,7 @@ typedef struct mpdata_opts {
     int32_t periodic[3];    /* per axis x, y, z: 1 periodic (default), 0 rigid lid */
     int32_t dtype;          /* MPDATA_F32 (default) or MPDATA_F64 */
     int32_t path;           /* MPDATA_PATH_FUSED (default) or MPDATA_PATH_STAGES */
-    int32_t tile_x, tile_y; /* fused-kernel output tile.  FP32: 32x24 or 32x16 run the
+    int32_t tile_x, tile_y; /* fused-kernel output tile.  FP32: 32x28, 32x24 or 32x16 run the
                                two-column kernel (any nx), 24x24, 24x16, 16x16 the
                                one-column kernel; FP64: 16x16.  0 x 0 picks the tile
                                of least predicted step time for the grid on this

@@ -564,7 +564,9 @@ cudaError_t launch_pairs_batch(int nonosc, int lid, const BatchGrid *grids, cons
 
 bool fused_pairs_supported(const Grid &g, int tx, int ty) {
     (void)g;  // any nx: 16-byte loads when nx % 4 == 0, 4-byte loads otherwise
-    return tx == 32 && (ty == 16 || ty == 24);
+    // 16 and 24 rows: 360 / 504 threads at up to 128 registers; 28 rows: 576
+    // threads (18 warps) at 96 registers, which hides latency better
+    return tx == 32 && (ty == 16 || ty == 24 || ty == 28);
 }
 
 cudaError_t launch_fused_pairs(const Grid &g, int nonosc, double eps, int tx, int ty, const void *h,
@@ -572,6 +574,7 @@ cudaError_t launch_fused_pairs(const Grid &g, int nonosc, double eps, int tx, in
                                void *out, cudaStream_t s) {
     if (tx == 32 && ty == 16) return launch_pairs<32, 16>(g, nonosc, eps, h, psi, u1, u2, u3, out, s);
     if (tx == 32 && ty == 24) return launch_pairs<32, 24>(g, nonosc, eps, h, psi, u1, u2, u3, out, s);
+    if (tx == 32 && ty == 28) return launch_pairs<32, 28>(g, nonosc, eps, h, psi, u1, u2, u3, out, s);
     return cudaErrorInvalidValue;
 }
 

@@ -190,7 +190,7 @@ def tune_grid(nx, ny, nz, periodic=(1, 1, 0), steps=10, tiles=((32, 24), (32, 16
     return report
 
 
-TILES = ((32, 24), (32, 16), (24, 24), (24, 16), (16, 16))
+TILES = ((32, 28), (32, 24), (32, 16), (24, 24), (24, 16), (16, 16))
 
 
 def probe_grids(count=40, seed=1511):

@@ -69,7 +69,7 @@ def test_edge_shapes_f64(nx, ny, nz, per, nonosc):
 
 
 @pytest.mark.parametrize("nx,ny,nz,per", EDGE)
-@pytest.mark.parametrize("tile", [None, (24, 24), (16, 16), (32, 16), (32, 24)])
+@pytest.mark.parametrize("tile", [None, (24, 24), (16, 16), (32, 16), (32, 24), (32, 28)])
 def test_edge_shapes_f32(nx, ny, nz, per, tile):
     f = rand_problem((nz, ny, nx), seed=nx * 17 + ny * 5 + nz, periodic=per)
     want = run_oracle(f, 3)
@@ -82,6 +82,8 @@ def test_edge_shapes_f32(nx, ny, nz, per, tile):
 def test_pair_kernel_matches_single_column_kernel(per, nx):
     f = rand_problem((12, 40, nx), seed=21, periodic=per)
     a = run_gpu(f, 6, tile=(32, 24))   # two columns per thread
+    a28 = run_gpu(f, 6, tile=(32, 28))
+    assert np.array_equal(a, a28)      # same arithmetic whatever the tile
     b = run_gpu(f, 6, tile=(24, 24))   # one column per thread
     assert rel_err(a, b) <= 1e-6
 
