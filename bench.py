@@ -296,7 +296,7 @@ def run_tracers(args):
     from paper_1507_01265_gb300 import tune
     pairs = every
     rates = {}
-    for ty in (24, 16):
+    for ty in (24, 16, 28):
         ms = time_batch(pairs, tile=(32, ty))
         work = sum(math.ceil(fs[i].nx / 32) * math.ceil(fs[i].ny / ty) * 32 * ty * (fs[i].nz + 3)
                    for i in pairs)
@@ -334,7 +334,7 @@ def run_tracers(args):
                                "ms_per_step": res["per_grid_tiles"],
                                "grids": len(pairs),
                                "tile_y_counts": {str(ty): sum(1 for i in pairs if chosen[i] == ty)
-                                                 for ty in (24, 16)},
+                                                 for ty in (24, 16, 28)},
                                "rates_cell_planes_per_s": {str(k): v for k, v in rates.items()}}}
     print(json.dumps(line), flush=True)
     return 0

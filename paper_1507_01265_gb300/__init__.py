@@ -161,14 +161,14 @@ class Batch:
     (mpdata_batch_*).  `grids` is a list of (nx, ny, nz) or (nx, ny, nz,
     (px, py, pz)); fields are attached per grid with set_fields."""
 
-    # 0/1: two-column 32x24 (x/y periodic / a lid), 2: one-column 32x16,
-    # 3/4: two-column 32x16 (x/y periodic / a lid)
-    VARIANTS = 5
+    # 0/1: two-column 32x24 (x/y periodic / a lid), 2: reserved (empty),
+    # 3/4: two-column 32x16, 5/6: two-column 32x28
+    VARIANTS = 7
 
     def __init__(self, grids, *, nonoscillatory: bool = True, tile=(32, 24), eps: float = 1e-15,
                  periodic=(1, 1, 1), tiles=None):
         """tile: the default tile; tiles: optional per-grid tile heights
-        (16, 24, or 0 for the default)."""
+        (16, 24, 28, or 0 for the default)."""
         o = _lib.default_opts()
         o.nonoscillatory = int(bool(nonoscillatory))
         o.tile_x, o.tile_y = int(tile[0]), int(tile[1])

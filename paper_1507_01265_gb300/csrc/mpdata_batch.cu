@@ -35,11 +35,17 @@ enum Variant {
     kSingle = 2,           // reserved (no FP32 grid needs the one-column kernel)
     kPairs16Periodic = 3,  // two columns per thread, tile 32x16
     kPairs16Lid = 4,
-    kNumVariants = 5
+    kPairs28Periodic = 5,  // two columns per thread, tile 32x28
+    kPairs28Lid = 6,
+    kNumVariants = 7
 };
 
-int variant_tile_y(int v) { return (v == kPairs24Periodic || v == kPairs24Lid) ? 24 : 16; }
-bool variant_lid(int v) { return v == kPairs24Lid || v == kPairs16Lid; }
+int variant_tile_y(int v) {
+    if (v == kPairs24Periodic || v == kPairs24Lid) return 24;
+    if (v == kPairs28Periodic || v == kPairs28Lid) return 28;
+    return 16;
+}
+bool variant_lid(int v) { return v == kPairs24Lid || v == kPairs16Lid || v == kPairs28Lid; }
 
 struct Group {
     std::vector<int2> items;  // (grid, tile)
@@ -170,11 +176,12 @@ int mpdata_batch_create_tiles(int ngrids, const int *dims, const int *periodic, 
                                     "extrema set and pure precision");
     if (!(o.eps > 0.0)) return bfail(MPDATA_EINVAL, "eps must be > 0");
     const int tx = o.tile_x ? o.tile_x : 32, ty_default = o.tile_y ? o.tile_y : 24;
-    if (!(tx == 32 && (ty_default == 16 || ty_default == 24))) return bfail(MPDATA_EINVAL, "batch tile must be 32x16 or 32x24");
+    if (!(tx == 32 && (ty_default == 16 || ty_default == 24 || ty_default == 28)))
+        return bfail(MPDATA_EINVAL, "batch tile must be 32x16, 32x24 or 32x28");
     if (tile_y)
         for (int i = 0; i < ngrids; ++i)
-            if (tile_y[i] != 0 && tile_y[i] != 16 && tile_y[i] != 24)
-                return bfail(MPDATA_EINVAL, "tile_y[%d] = %d: must be 0 (the batch default), 16 or 24", i, tile_y[i]);
+            if (tile_y[i] != 0 && tile_y[i] != 16 && tile_y[i] != 24 && tile_y[i] != 28)
+                return bfail(MPDATA_EINVAL, "tile_y[%d] = %d: must be 0 (the batch default), 16, 24 or 28", i, tile_y[i]);
 
     mpdata_batch *b = new (std::nothrow) mpdata_batch();
     if (!b) return bfail(MPDATA_ENOMEM, "host allocation failed");
@@ -206,7 +213,9 @@ int mpdata_batch_create_tiles(int ngrids, const int *dims, const int *periodic, 
         g.eps = (float)o.eps;
         const int ty = (tile_y && tile_y[i]) ? tile_y[i] : ty_default;
         const bool lid = !g.g.per[0] || !g.g.per[1];
-        const int v = ty == 24 ? (lid ? kPairs24Lid : kPairs24Periodic) : (lid ? kPairs16Lid : kPairs16Periodic);
+        const int v = ty == 24 ? (lid ? kPairs24Lid : kPairs24Periodic)
+                      : ty == 28 ? (lid ? kPairs28Lid : kPairs28Periodic)
+                                 : (lid ? kPairs16Lid : kPairs16Periodic);
         g.ntx = (nx + tx - 1) / tx;
         const int ntiles = g.ntx * ((ny + ty - 1) / ty);
         b->variant[i] = v;

@@ -583,6 +583,7 @@ cudaError_t launch_fused_pairs_batch(int tx, int ty, int nonosc, int lid, const 
                                      cudaStream_t s) {
     if (tx == 32 && ty == 16) return launch_pairs_batch<32, 16>(nonosc, lid, grids, items, begin, ncta, parity, s);
     if (tx == 32 && ty == 24) return launch_pairs_batch<32, 24>(nonosc, lid, grids, items, begin, ncta, parity, s);
+    if (tx == 32 && ty == 28) return launch_pairs_batch<32, 28>(nonosc, lid, grids, items, begin, ncta, parity, s);
     return cudaErrorInvalidValue;
 }
 

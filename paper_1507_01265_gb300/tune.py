@@ -112,11 +112,12 @@ def split_time(costs, nsm):
     return max(prefix[begin[c + 1]] - prefix[begin[c]] for c in range(ncta))
 
 
-def batch_time(dims, tiles, rates, nsm, launch_s=5e-6, tx=32):
+def batch_time(dims, tiles, rates, nsm, launch_s=50e-6, tx=32):
     """Predicted time of one batched step: one persistent launch per tile
     shape in use (items in batch order, default split), a tile of shape ty
     costing tx*ty*(nz+3) cell-planes at rates[ty] / nsm per CTA, plus
-    launch_s per launch."""
+    launch_s per launch (a persistent launch's fill and drain: a second
+    shape's launch measured about 60 us per step on the tracer batch)."""
     items = {}
     for (nx, ny, nz), ty in zip(dims, tiles):
         tile_s = tx * ty * (nz + 3) / (rates[ty] / nsm)
@@ -124,7 +125,7 @@ def batch_time(dims, tiles, rates, nsm, launch_s=5e-6, tx=32):
     return sum(split_time(c, nsm) + launch_s for c in items.values())
 
 
-def choose_tiles(dims, rates, nsm, launch_s=5e-6):
+def choose_tiles(dims, rates, nsm, launch_s=50e-6):
     """Per-grid tile heights (keys of `rates`, e.g. {24: r24, 16: r16}) for
     the grids dims = [(nx, ny, nz), ...]: the best of the uniform choices and
     of every grid taking its own cheapest shape, then single-grid switches

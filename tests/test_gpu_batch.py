@@ -93,14 +93,14 @@ def test_per_grid_tiles(mp, graph):
     single-grid run with that tile, and the grids land in the documented
     variants."""
     import torch
-    tiles = [16, 24, 0, 16, 24, 16, 0]
+    tiles = [16, 24, 0, 28, 24, 16, 28]
     fs = [rand_problem((nz, ny, nx), seed=i + 80, periodic=per) for i, (nx, ny, nz, per) in enumerate(MIX)]
     ts = _fields(mp, fs)
     with mp.Batch([(f.nx, f.ny, f.nz, f.periodic) for f in fs], tiles=tiles) as b:
         want = []
         for i, (f, ty) in enumerate(zip(fs, tiles)):
             lid = not (f.periodic[0] and f.periodic[1])
-            want.append((0 if (ty or 24) == 24 else 3) + int(lid))
+            want.append({24: 0, 16: 3, 28: 5}[ty or 24] + int(lid))
         assert [b.grid_variant(i) for i in range(len(fs))] == want
         for i, t in enumerate(ts):
             b.set_fields(i, *t)
