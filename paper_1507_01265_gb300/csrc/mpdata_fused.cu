@@ -434,9 +434,9 @@ void fused_default_tile(int dtype, const Grid &g, int nsm, int *tx, int *ty) {
     // smallest, fastest plane; a large one the most cells per plane-time.
     struct Cand { int tx, ty; double us_aligned, us_any; };
     static const Cand cands[] = {
-        {32, 24, 1.95, 2.69},  // two-column kernel (16-byte loads if nx % 4 == 0)
-        {32, 28, 2.28, 3.76},  // 18 warps at 96 registers: slow alone, fast in full waves
-        {32, 16, 1.56, 2.06},
+        {32, 24, 1.94, 2.27},  // two-column kernel (16-byte loads if nx % 4 == 0)
+        {32, 28, 2.28, 2.89},  // 18 warps at 96 registers: slow alone, fast in full waves
+        {32, 16, 1.56, 1.75},
         {24, 16, 1.86, 1.86},  // one-column kernel
         {16, 16, 1.51, 1.51},
     };

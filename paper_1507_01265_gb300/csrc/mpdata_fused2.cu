@@ -242,67 +242,76 @@ __device__ __forceinline__ void pairs_tile(const TileArgs &a, int tile, float *s
     auto rshF = [&](unsigned b, F2 own) { return make_float2(own.y, lds<8>(b)); };
     auto lid2 = [&](F2 v, bool a, bool c) { return make_float2(a ? 0.f : v.x, c ? 0.f : v.y); };
 
-    // ---- this thread's load chunk (4 columns of one row) of the radius-3 plane ----
+    // ---- this thread's share of the radius-3 plane loads ----
+    // nx % 4 == 0: one 16-byte chunk (4 columns of one row) per thread and
+    // field.  Any other nx: 4-byte copies of plane elements t, t + NT, ...,
+    // so that a warp reads 128 contiguous bytes and writes consecutive words.
+    constexpr int NE = (PL + L::NT - 1) / L::NT;  // 4-byte elements per thread and field
     const bool has_chunk = t < L::NCH;
-    int ld_off = 0, lx = 0;
-    bool z_all = false, z_u2 = false, z_row = false, y_face0 = false, patch_u1 = false, contig = true;
+    int ld_off = 0;
+    bool z_all = false, z_u2 = false, patch_u1 = false;
     unsigned ld_dst = 0;
-    if (has_chunk) {
-        const int ey = t / L::CPR, cc = t % L::CPR;
-        lx = x0 - 4 + 4 * cc;
-        const int ly = y0 - 3 + ey;
-        int cx, cy;
-        bool outx = false, outy = false;
-        if constexpr (AL == 1) {
+    int e_off[NE];
+    unsigned e_flags = 0;  // per element: bit 3r zero (lid ghost), 3r+1 y-lid face, 3r+2 x-lid face
+    if (a16) {
+        if (has_chunk) {
+            const int ey = t / L::CPR, cc = t % L::CPR;
+            const int lx = x0 - 4 + 4 * cc, ly = y0 - 3 + ey;
+            int cx, cy;
+            bool outx = false, outy = false;
             if (perx) cx = wrap(lx, nx); else { outx = lx < 0 || lx >= nx; cx = outx ? 0 : lx; }
             if (pery) cy = wrap(ly, ny); else { outy = ly < 0 || ly >= ny; cy = outy ? 0 : ly; }
-            z_all = outx || outy;                // lid ghost: never read as a cell value
-            z_u2 = z_all || (!pery && ly == 0);  // y-lid face 0
-        } else {
-            if (pery) cy = wrap(ly, ny); else { outy = ly < 0 || ly >= ny; cy = outy ? 0 : ly; }
-            if (a16) {
-                if (perx) cx = wrap(lx, nx); else { outx = lx < 0 || lx >= nx; cx = outx ? 0 : lx; }
-            } else {
-                contig = lx >= 0 && lx + 3 < nx;  // the 4 columns are consecutive in memory
-                cx = contig ? lx : 0;
-            }
-            z_row = outy;                         // y-lid ghost row
-            z_all = outx || outy;
-            y_face0 = !pery && ly == 0;
-            z_u2 = z_all || y_face0;
+            z_all = outx || outy;                    // lid ghost: never read as a cell value
+            z_u2 = z_all || (!pery && ly == 0);      // y-lid face 0
+            patch_u1 = LID && !perx && lx == 0;      // x-lid face 0 is this chunk's first element
+            ld_off = cy * nx + cx;
+            ld_dst = sm_base + (unsigned)(ey * EX + 4 * cc) * 4u;
         }
-        patch_u1 = LID && !perx && lx == 0;      // x-lid face 0 is this chunk's first element
-        ld_off = cy * nx + cx;
-        ld_dst = sm_base + (unsigned)(ey * EX + 4 * cc) * 4u;
+    } else {
+#pragma unroll
+        for (int r = 0; r < NE; ++r) {
+            const int idx = t + r * L::NT;
+            e_off[r] = 0;
+            if (idx < PL) {
+                const int lx = x0 - 4 + idx % EX, ly = y0 - 3 + idx / EX;
+                int cx, cy;
+                bool outx = false, outy = false;
+                if (perx) cx = wrap(lx, nx); else { outx = lx < 0 || lx >= nx; cx = outx ? 0 : lx; }
+                if (pery) cy = wrap(ly, ny); else { outy = ly < 0 || ly >= ny; cy = outy ? 0 : ly; }
+                e_off[r] = cy * nx + cx;
+                e_flags |= (unsigned)(outx || outy) << (3 * r);
+                e_flags |= (unsigned)(!pery && ly == 0) << (3 * r + 1);
+                e_flags |= (unsigned)(LID && !perx && lx == 0) << (3 * r + 2);
+            }
+        }
     }
     auto issue = [&](int p) {
-        if (has_chunk) {
-            const long long pc = (long long)(perz ? wrap(p, nz) : min(max(p, 0), nz - 1)) * nxy + ld_off;
-            const bool zz = !perz && (p <= 0 || p >= nz);  // z-lid face
-            const unsigned d = ld_dst + (unsigned)(slot5(p) * PB);
-            if (a16) {
+        if (a16) {
+            if (has_chunk) {
+                const long long pc = (long long)(perz ? wrap(p, nz) : min(max(p, 0), nz - 1)) * nxy + ld_off;
+                const bool zz = !perz && (p <= 0 || p >= nz);  // z-lid face
+                const unsigned d = ld_dst + (unsigned)(slot5(p) * PB);
                 cp16(d, psi + pc, z_all);
                 cp16(d + FB, u1 + pc, z_all);
                 cp16(d + 2 * FB, u2 + pc, z_u2);
                 cp16(d + 3 * FB, u3 + pc, z_all || zz);
                 cp16(d + 4 * FB, h + pc, z_all);
-            } else {
+            }
+        } else {
+            const long long pz = (long long)(perz ? wrap(p, nz) : min(max(p, 0), nz - 1)) * nxy;
+            const bool zz = !perz && (p <= 0 || p >= nz);  // z-lid face
+            const unsigned d0 = sm_base + (unsigned)(t * 4 + slot5(p) * PB);
 #pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    long long o = pc + e;
-                    bool ze = z_row;
-                    if (!contig) {  // crosses the x wrap or an x lid: map this column
-                        const int x = lx + e;
-                        int c;
-                        if (perx) c = wrap(x, nx); else { ze = ze || x < 0 || x >= nx; c = (x < 0 || x >= nx) ? 0 : x; }
-                        o = pc + c;
-                    }
-                    const unsigned de = d + 4u * e;
-                    cp4(de, psi + o, ze);
-                    cp4(de + FB, u1 + o, ze);
-                    cp4(de + 2 * FB, u2 + o, ze || y_face0);
-                    cp4(de + 3 * FB, u3 + o, ze || zz);
-                    cp4(de + 4 * FB, h + o, ze);
+            for (int r = 0; r < NE; ++r) {
+                if (t + r * L::NT < PL) {
+                    const long long o = pz + e_off[r];
+                    const unsigned d = d0 + (unsigned)(r * L::NT * 4);
+                    const bool ze = (e_flags >> (3 * r)) & 1u;
+                    cp4(d, psi + o, ze);
+                    cp4(d + FB, u1 + o, ze || ((e_flags >> (3 * r + 2)) & 1u));
+                    cp4(d + 2 * FB, u2 + o, ze || ((e_flags >> (3 * r + 1)) & 1u));
+                    cp4(d + 3 * FB, u3 + o, ze || zz);
+                    cp4(d + 4 * FB, h + o, ze);
                 }
             }
         }
