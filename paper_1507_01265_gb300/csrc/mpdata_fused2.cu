@@ -1,20 +1,27 @@
 // Fused MPDATA step, FP32, two adjacent x-columns per thread.
 //
-// The same stage schedule as mpdata_fused.cu (a CTA marches a TX x TY tile
-// through z; per plane p: donor pass at p-1 | x/y pseudo-velocities at p-2 |
-// z-face pseudo-velocity and limiter factors at p-2 | limited corrective
-// fluxes at p-2 and the output of p-3), with three changes aimed at the
-// instruction count, which is what bounds this step on GB300:
+// A CTA marches a TX x TY tile through z (TX = 32; TY = 16, 24 or 28).  Per
+// iteration p, with q1 = p-1, q2 = p-2, q3 = p-3, three barriers:
+//   alpha  donor pass of q1 completed from the neighbours' fluxes (a1), pair
+//          sums for the cross terms, x/y pseudo-velocities at q2 (a2);
+//   beta   z-face pseudo-velocity, local extrema and limiter factors at q2
+//          (a2-a4);
+//   gamma  limited velocities and corrective fluxes at q2, output of q3
+//          (a5-a6), and the donor fluxes of plane p (work for the warps that
+//          the flux stage leaves idle).
+// Inputs (psi, u1, u2, u3, h) load two planes ahead into a 5-plane ring.
+// Aimed at the instruction count and latency, which bound this step on GB300:
 //   * each thread owns a pair of adjacent columns (i, i+1) and evaluates both
 //     with packed f32x2 add/mul/fma, so per-thread overhead (addressing,
 //     predicates, loop control) is paid once per two cells and shared-memory
-//     neighbours of the pair come in one 64-bit load;
+//     neighbours of the pair come in one 64-bit load; the plane loop is
+//     unrolled by two so that register queues shift by renaming;
 //   * inputs stream in as 16-byte cp.async chunks when nx is a multiple of 4
 //     (chunks then never straddle a wrap or a lid and rows stay 16-byte
-//     aligned); for any other nx the same chunks move as four 4-byte copies,
-//     element by element where a chunk crosses the x wrap or lid.  Columns
-//     past nx are ghosts: wrapped copies on a periodic axis, zero-filled faces
-//     and clamped cell values behind a lid, never stored;
+//     aligned); for any other nx as 4-byte copies in element order (a warp
+//     copies 128 contiguous bytes).  Columns past nx are ghosts: wrapped
+//     copies on a periodic axis, zero-filled faces and clamped cell values
+//     behind a lid, never stored;
 //   * when x and y are both periodic (LID = false) every neighbour offset is
 //     a compile-time constant; with a lid on x or y (LID = true) the neighbour
 //     reads of cell fields are clamped (zero-gradient ghosts) and the lid

@@ -318,3 +318,24 @@ def test_courant_max_closed_forms():
     t = [torch.from_numpy(a).cuda() for a in [h] + uz]
     with mp.Solver(nx, ny, nz, periodic=(1, 1, 0)) as s:
         assert s.courant_max(*t) == 0.0
+
+
+def test_default_tile_choice():
+    """The default tile follows the predicted step time: the two-column
+    kernel with 32x28 tiles for the 1024x512 grid (608 tiles, four full
+    waves on 152 SMs), the smallest one-column tile for a grid too small to
+    fill the GPU, 16x16 for FP64."""
+    import torch
+    import paper_1507_01265_gb300 as mp
+    nsm = torch.cuda.get_device_properties(0).multi_processor_count
+    with mp.Solver(40, 24, 12) as s:
+        assert s.tile == (16, 16)
+    with mp.Solver(64, 64, 8, dtype="f64") as s:
+        assert s.tile == (16, 16)
+    with mp.Solver(64, 64, 8, path="stages") as s:
+        assert s.tile == (0, 0)
+    if nsm == 152:
+        with mp.Solver(1024, 512, 64, periodic=(1, 1, 0)) as s:
+            assert s.tile == (32, 28)
+        with mp.Solver(4096, 2048, 32, periodic=(1, 1, 0)) as s:
+            assert s.tile == (32, 24)
