@@ -102,11 +102,20 @@ def measured_peaks():
 FUSED_SOURCES = ("mpdata_fused2.cu", "mpdata_fused.cu", "mpdata_internal.cuh")
 
 
+def _code_only(text):
+    """C++ source without comments and blank lines (a comment edit does not
+    change the kernel)."""
+    import re
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    lines = (re.sub(r"//.*$", "", ln).rstrip() for ln in text.splitlines())
+    return "\n".join(ln for ln in lines if ln)
+
+
 def fused_source_sha256():
     h = hashlib.sha256()
     for name in FUSED_SOURCES:
-        with open(os.path.join(ROOT, "paper_1507_01265_gb300", "csrc", name), "rb") as f:
-            h.update(f.read())
+        with open(os.path.join(ROOT, "paper_1507_01265_gb300", "csrc", name)) as f:
+            h.update(_code_only(f.read()).encode())
     return h.hexdigest()
 
 
