@@ -256,6 +256,28 @@ def test_rotation_blobs_full_size_sampled(nsteps):
     assert np.abs(vals - want).max() <= 1e-5 * scale
 
 
+@pytest.mark.parametrize("nx,ny,per,tile", [
+    (1021, 509, (1, 1, 0), (32, 24)),   # odd nx: 4-byte loads, ghost column wraps
+    (1022, 510, (0, 1, 0), (32, 28)),   # nx % 4 == 2 with an x lid
+    (1021, 512, (1, 0, 0), None),       # odd nx with a y lid, default tile
+])
+def test_ragged_full_size_sampled(nx, ny, per, tile):
+    """Full-size grids whose nx is not a multiple of 4 (the 4-byte load path
+    and the per-column stores), sampled against the oracle, with the cells
+    next to the x edges always among the samples."""
+    f = F.rotation_blobs(nx=nx, ny=ny, nz=64, periodic=per, nsteps=2)
+    got = run_gpu(f, 2, tile=tile)
+    r = np.random.default_rng(nx + ny)
+    samples = [(int(r.integers(f.nz)), int(r.integers(f.ny)), int(r.integers(f.nx)))
+               for _ in range(80)]
+    for i in (0, 1, 2, nx - 3, nx - 2, nx - 1):
+        samples.append((int(r.integers(f.nz)), int(r.integers(f.ny)), i))
+    samples += [(0, 0, 0), (f.nz - 1, f.ny - 1, f.nx - 1)]
+    want = oracle_at(f, samples, 2)
+    vals = np.array([got[s] for s in samples])
+    assert np.abs(vals - want).max() <= 1e-5 * float(np.abs(f.psi).max())
+
+
 def test_rotation_blobs_full_size_invariants():
     import torch
     import paper_1507_01265_gb300 as mp
