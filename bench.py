@@ -46,6 +46,14 @@ NX, NY, NZ, NSTEPS = 1024, 512, 64, 50
 FIELDS = 6  # read psi, h, u1, u2, u3; write psi
 
 
+def workload_config():
+    """The grid workload both arms report (the native arm adds its kernel
+    choice, the reference arm its sample)."""
+    return {"workload": "rotation_blobs 1024x512x64, periodic x/y, lid z, 50 MPDATA steps per solve",
+            "grid": [NX, NY, NZ], "mpdata_steps_per_step": NSTEPS, "iterations": 2,
+            "nonoscillatory": True}
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -258,8 +266,8 @@ def run_reference(args, rank, world):
             "warmup": args.warmup, "ms_per_step": 1e3 * t / len(times), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "impl": "reference",
-            "config": {"workload": "rotation_blobs 1024x512x64, periodic x/y, lid z (sampled slab)",
-                       "grid": [NX, NY, NZ], "sample_grid": [cfg.nx, rows, cfg.nz]},
+            "config": dict(workload_config(), sample_grid=[cfg.nx, rows, cfg.nz],
+                           parallelism="host cores"),
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -650,13 +658,9 @@ def main():
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "rotation_blobs 1024x512x64, periodic x/y, lid z, "
-                                   "50 MPDATA steps per solve",
-                       "grid": [NX, NY, NZ], "mpdata_steps_per_step": NSTEPS,
-                       "path": args.path, "tile": list(solver.tile),
-                       "iterations": 2, "nonoscillatory": True,
-                       "l2": "inputs 671 MB + output 134 MB per launch > 129 MB L2 (no flush)",
-                       "parallelism": "replicas" if world > 1 else "single"},
+            "config": dict(workload_config(), path=args.path, tile=list(solver.tile),
+                           l2="inputs 671 MB + output 134 MB per launch > 129 MB L2 (no flush)",
+                           parallelism="replicas" if world > 1 else "single"),
             "roofline": roofline, "e2e": e2e, "cpu_baseline": cpu,
             "clocks": clk.summary(), "gpu_launches": launches,
             "pct_hbm_roofline": 100.0 * roofline["frac"],
