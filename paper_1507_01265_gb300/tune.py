@@ -155,7 +155,7 @@ def choose_tiles(dims, rates, nsm, launch_s=50e-6):
     return best
 
 
-def tune_grid(nx, ny, nz, periodic=(1, 1, 0), steps=10, tiles=((32, 24), (32, 16)), xs_max=10):
+def tune_grid(nx, ny, nz, periodic=(1, 1, 0), steps=10, tiles=((32, 28), (32, 24), (32, 16)), xs_max=10):
     """Speed functions per tile shape, the partitioner's choice, and measured
     step times of the balanced and the chosen split on this grid."""
     P = num_sms()
