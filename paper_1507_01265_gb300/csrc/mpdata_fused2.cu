@@ -77,7 +77,6 @@ __device__ __forceinline__ F2 min3(F2 a, F2 b, F2 c) {
 __device__ __forceinline__ F2 flux(F2 U, F2 L, F2 R) {
     return mul(U, make_float2(U.x > 0.f ? L.x : R.x, U.y > 0.f ? L.y : R.y));
 }
-__device__ __forceinline__ F2 ld2(const float *p) { return *reinterpret_cast<const F2 *>(p); }
 __device__ __forceinline__ void st2(float *p, F2 v) { *reinterpret_cast<F2 *>(p) = v; }
 
 // Pseudo-velocity of both faces of the pair (see mpdata_fused.cu):
