@@ -107,7 +107,7 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
-FUSED_SOURCES = ("mpdata_fused2.cu", "mpdata_fused.cu", "mpdata_internal.cuh")
+FUSED_SOURCES = ("mpdata_fused2.cu", "mpdata_internal.cuh")  # the two-column kernel's code
 
 
 def _code_only(text):

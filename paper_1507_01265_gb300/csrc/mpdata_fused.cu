@@ -228,6 +228,9 @@ __device__ __forceinline__ void single_tile(const Grid &g, T eps, int ntx, const
     T dacc = T(0), gx_own = T(0), gy_own = T(0);
 
     issue(p_first);
+    // FP32: unrolled by two so that the register queues shift by renaming
+    // (FP64 would spill)
+#pragma unroll(sizeof(T) == 4 ? 2 : 1)
     for (int p = p_first; p <= p_last; ++p) {
         const int q1 = p - 1, q2 = p - 2, q3 = p - 3;
         if (p + 1 <= p_last) issue(p + 1); else cp_async_commit();
@@ -437,8 +440,8 @@ void fused_default_tile(int dtype, const Grid &g, int nsm, int *tx, int *ty) {
         {32, 24, 1.94, 2.27},  // two-column kernel (16-byte loads if nx % 4 == 0)
         {32, 28, 2.28, 2.89},  // 18 warps at 96 registers: slow alone, fast in full waves
         {32, 16, 1.56, 1.75},
-        {24, 16, 1.86, 1.86},  // one-column kernel
-        {16, 16, 1.51, 1.51},
+        {24, 16, 1.76, 1.76},  // one-column kernel
+        {16, 16, 1.45, 1.45},
     };
     const int sms = nsm > 0 ? nsm : 1 << 30;  // unknown device: every grid is one wave
     double best = 0.0;
