@@ -127,18 +127,23 @@ def fused_source_sha256():
     return h.hexdigest()
 
 
-def kernel_traffic(ncells):
-    """DRAM bytes per launch of the fused kernel from the committed ncu
-    summary, valid only while the kernel sources are unchanged."""
+def kernel_record():
+    """The committed ncu record of the fused kernel (DRAM bytes and warp
+    instructions per cell), or None once the kernel code has changed."""
     path = os.path.join(ROOT, "profiles", "fused_traffic.json")
     try:
         with open(path) as f:
             rec = json.load(f)
-        if rec.get("source_sha256") != fused_source_sha256():
-            return None
-        return float(rec["bytes_per_cell"]) * ncells
+        return rec if rec.get("source_sha256") == fused_source_sha256() else None
     except Exception:
         return None
+
+
+def kernel_traffic(ncells):
+    """DRAM bytes per launch of the fused kernel from the committed ncu
+    summary, valid only while the kernel sources are unchanged."""
+    rec = kernel_record()
+    return None if rec is None else float(rec["bytes_per_cell"]) * ncells
 
 
 class ClockSampler:
@@ -636,6 +641,16 @@ def main():
                 "frac": achieved / peak, "traffic": kernel_traffic(ncells),
                 "peak_kind": peak_kind, "kernel": "k_fused" if args.path == "fused" else "stage kernels",
                 "algorithmic_bytes_per_launch": algo_bytes}
+    rec = kernel_record() if args.path == "fused" else None
+    if rec is not None and "warp_inst_per_cell" in rec:
+        # what binds the kernel: instruction issue (one warp instruction per
+        # scheduler per cycle; 4 schedulers per SM)
+        nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+        issue_peak = nsm * 4 * 2070e6 / 1e9
+        issue_ach = rec["warp_inst_per_cell"] * ncells / launch_s / 1e9
+        roofline["issue"] = {"achieved": issue_ach, "peak": issue_peak, "unit": "G warp-inst/s",
+                             "frac": issue_ach / issue_peak,
+                             "warp_inst_per_cell": rec["warp_inst_per_cell"]}
 
     # end to end through the public host API
     e2e = None
