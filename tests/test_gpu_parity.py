@@ -361,3 +361,17 @@ def test_default_tile_choice():
             assert s.tile == (32, 28)
         with mp.Solver(4096, 2048, 32, periodic=(1, 1, 0)) as s:
             assert s.tile == (32, 24)
+
+
+@pytest.mark.parametrize("nx,ny,nz,per", [
+    (8192, 2, 3, (1, 1, 0)),    # a thin slab: the y halo wraps several times
+    (2, 4000, 5, (0, 1, 1)),    # a narrow column: every pair straddles the x lid
+    (4, 4, 3000, (1, 1, 0)),    # a long z-march
+    (3, 1, 2000, (1, 1, 1)),
+])
+def test_extreme_aspect_ratios(nx, ny, nz, per):
+    f = rand_problem((nz, ny, nx), seed=nx + 7 * ny + 3 * nz, periodic=per)
+    want = run_oracle(f, 2)
+    for tile in (None, (32, 28)):
+        assert rel_err(run_gpu(f, 2, tile=tile), want) <= 1e-5, tile
+    assert rel_err(run_gpu(f, 2, dtype="f64"), want) <= 1e-12
