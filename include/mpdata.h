@@ -136,6 +136,41 @@ int mpdata_step(mpdata_t *handle, const void *h, void *psi, const void *u1, cons
 int mpdata_solve_host(mpdata_t *handle, const void *h, void *psi, const void *u1,
                       const void *u2, const void *u3, int nsteps, void *stream);
 
+/* Pipelined solves on HOST arrays: the §5.2 step loop of mpdata_solve_host
+ * for a sequence of independent problems (one problem after another through
+ * one device, each on its own fields), with the copies of one solve
+ * overlapping the steps of its neighbours.  Enqueues without blocking the
+ * host: the copy of h, psi_in, u1, u2, u3 into one of two device slots owned
+ * by the handle (on a copy-in stream of the handle), nsteps steps of that slot
+ * on `stream`, and the copy of the result to psi_out (on a copy-out stream of
+ * the handle).  Consecutive submits alternate slots; the steps of all solves
+ * run in submit order on `stream`; the copy into a slot waits until the solve
+ * that used the slot two submits earlier has been copied out.
+ * Host arrays: nx*ny*nz elements of the handle's dtype.  Page-locked memory
+ * (cudaHostAlloc, cudaHostRegister, torch pin_memory) is needed for the
+ * copies to overlap; pageable memory gives correct results but the copies
+ * then block the host.  Ownership: the caller keeps all six arrays valid,
+ * the five inputs unmodified and psi_out unread and unwritten, until
+ * mpdata_host_wait on this solve's ticket (or a later one) has returned.
+ * psi_out may be psi_in of the same submit.  Solves in flight may share
+ * input arrays; psi_out must not overlap an input of another solve in
+ * flight, and when several solves in flight write the same psi_out the
+ * latest submit's result is what remains (the copies out run in submit
+ * order).
+ * *ticket receives the solve's id: 1 for the handle's first submit, then
+ * increasing by one.
+ * Errors: EINVAL (null argument, nsteps < 0), ENOMEM, ECUDA. */
+int mpdata_host_submit(mpdata_t *handle, const void *h, const void *psi_in, const void *u1,
+                       const void *u2, const void *u3, int nsteps, void *psi_out, void *stream,
+                       unsigned long long *ticket);
+
+/* Block the calling thread until solve `ticket` of this handle has written
+ * psi_out; every earlier solve has then finished too (the copies out run in
+ * submit order).  A ticket that has already been waited for returns at once.
+ * Errors: ENOENT (ticket 0 or not yet issued), ECUDA (a copy or a step of
+ * this or an earlier solve failed). */
+int mpdata_host_wait(mpdata_t *handle, unsigned long long ticket);
+
 /* Diagnostics (async; the paper defines none: sum h*psi is the quantity the
  * flux form of the §5.2 scheme conserves): out3[0] = sum of h*psi over all cells, out3[1] =
  * min psi, out3[2] = max psi, written as three doubles to the DEVICE

@@ -59,6 +59,7 @@ class Solver:
         self.dtype_name = dtype
         self.opts = o
         self._h = ctypes.c_void_p()
+        self._inflight = {}  # ticket -> host arrays of a submit_host not yet waited for
         check(_lib.lib.mpdata_create(self.nx, self.ny, self.nz, ctypes.byref(o),
                                      ctypes.byref(self._h)), "mpdata_create")
 
@@ -90,25 +91,48 @@ class Solver:
         check(_lib.lib.mpdata_step(self._h, *args, int(nsteps), _stream_handle(stream)),
               "mpdata_step")
 
+    def _host_ptr(self, a, name):
+        import numpy as np
+        torch = _torch()
+        if isinstance(a, torch.Tensor):
+            if a.is_cuda or not a.is_contiguous() or a.dtype != self.torch_dtype() or a.numel() != self.ncells:
+                raise ValueError("%s must be a contiguous CPU tensor of %d %s elements"
+                                 % (name, self.ncells, self.torch_dtype()))
+            return ctypes.c_void_p(a.data_ptr())
+        want = np.float64 if self.dtype_name == "f64" else np.float32
+        if a.dtype != want or not a.flags.c_contiguous or a.size != self.ncells:
+            raise ValueError("%s must be a contiguous %s array of %d elements"
+                             % (name, np.dtype(want).name, self.ncells))
+        return ctypes.c_void_p(a.ctypes.data)
+
     def solve_host(self, h, psi, u1, u2, u3, nsteps: int, stream=None) -> None:
         """nsteps steps on host arrays (numpy or CPU tensors); psi is updated
         in place.  Copies in, steps and copies back inside the call."""
-        import numpy as np
-        torch = _torch()
-        ptrs = []
-        want = np.float64 if self.dtype_name == "f64" else np.float32
-        for a, n in ((h, "h"), (psi, "psi"), (u1, "u1"), (u2, "u2"), (u3, "u3")):
-            if isinstance(a, torch.Tensor):
-                if a.is_cuda or not a.is_contiguous() or a.dtype != self.torch_dtype():
-                    raise ValueError("%s must be a contiguous CPU tensor of %s" % (n, self.torch_dtype()))
-                ptrs.append(ctypes.c_void_p(a.data_ptr()))
-            else:
-                if a.dtype != want or not a.flags.c_contiguous or a.size != self.ncells:
-                    raise ValueError("%s must be a contiguous %s array of %d elements"
-                                     % (n, np.dtype(want).name, self.ncells))
-                ptrs.append(ctypes.c_void_p(a.ctypes.data))
+        ptrs = [self._host_ptr(a, n) for a, n in ((h, "h"), (psi, "psi"), (u1, "u1"), (u2, "u2"), (u3, "u3"))]
         check(_lib.lib.mpdata_solve_host(self._h, *ptrs, int(nsteps), _stream_handle(stream)),
               "mpdata_solve_host")
+
+    def submit_host(self, h, psi, u1, u2, u3, nsteps: int, psi_out=None, stream=None) -> int:
+        """Enqueue one solve of nsteps steps on host arrays and return its
+        ticket at once; the copies of consecutive solves overlap each other's
+        steps (page-locked arrays, e.g. torch pin_memory(), are needed for
+        that).  The result lands in psi_out (default: psi) once
+        wait_host(ticket) has returned; until then the arrays must not be
+        touched.  The solver keeps references to them until that wait."""
+        out = psi if psi_out is None else psi_out
+        arrays = (h, psi, u1, u2, u3, out)
+        ptrs = [self._host_ptr(a, n) for a, n in zip(arrays, ("h", "psi", "u1", "u2", "u3", "psi_out"))]
+        t = ctypes.c_ulonglong()
+        check(_lib.lib.mpdata_host_submit(self._h, *ptrs[:5], int(nsteps), ptrs[5],
+                                          _stream_handle(stream), ctypes.byref(t)), "mpdata_host_submit")
+        self._inflight[t.value] = arrays
+        return t.value
+
+    def wait_host(self, ticket: int) -> None:
+        """Block until solve `ticket` (and every earlier one) has written its psi_out."""
+        check(_lib.lib.mpdata_host_wait(self._h, int(ticket)), "mpdata_host_wait")
+        for k in [k for k in self._inflight if k <= ticket]:
+            del self._inflight[k]
 
     @property
     def tile(self):
@@ -140,8 +164,9 @@ class Solver:
 
     def close(self) -> None:
         if getattr(self, "_h", None) is not None and self._h.value:
-            _lib.lib.mpdata_destroy(self._h)
+            _lib.lib.mpdata_destroy(self._h)  # waits for the pipelined host solves
             self._h = ctypes.c_void_p()
+            self._inflight = {}
 
     def __del__(self):
         try:

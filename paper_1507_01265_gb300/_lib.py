@@ -79,6 +79,8 @@ def _load():
         "mpdata_get_tile": (I, [H, ctypes.POINTER(I), ctypes.POINTER(I)]),
         "mpdata_step": (I, [H, P, P, P, P, P, I, P]),
         "mpdata_solve_host": (I, [H, P, P, P, P, P, I, P]),
+        "mpdata_host_submit": (I, [H, P, P, P, P, P, I, P, P, ctypes.POINTER(ctypes.c_ulonglong)]),
+        "mpdata_host_wait": (I, [H, ctypes.c_ulonglong]),
         "mpdata_mass": (I, [H, P, P, P, P]),
         "mpdata_mass_noalloc": (I, [P, P, ctypes.c_longlong, I, P, P]),
         "mpdata_courant_max": (I, [H, P, P, P, P, P, P]),

@@ -23,7 +23,15 @@ struct mpdata_handle {
     void *scratch;            // psi-sized ping-pong partner
     mpdata::StageBuffers st;  // stage-per-kernel intermediates (path STAGES only)
     double *partials;         // mass reduction partials (kReduceBlocks x 3)
-    void *host_fields[5];     // device copies for mpdata_solve_host (lazy)
+    void *host_fields[5];     // device copies for mpdata_solve_host (lazy); slot 0 of the pipeline
+    // mpdata_host_submit pipeline (created on the first submit)
+    bool pipe_ready;
+    void *pipe_fields[5];     // slot 1
+    cudaStream_t pipe_in, pipe_out;
+    cudaEvent_t loaded[2], stepped[2], freed[2];  // per slot
+    cudaEvent_t done[16];                         // per ticket, ring of 16
+    bool slot_used[2];
+    unsigned long long issued, waited;
 };
 
 namespace {
@@ -77,8 +85,23 @@ int check_opts(const mpdata_opts *o) {
     return MPDATA_OK;
 }
 
+constexpr int kDoneRing = 16;
+
 void free_handle(mpdata_t *m) {
     if (!m) return;
+    if (m->pipe_ready) {
+        // the last copy out ends after every pipelined copy and step
+        if (m->issued) cudaEventSynchronize(m->done[m->issued % kDoneRing]);
+        for (int i = 0; i < 2; ++i) {
+            cudaEventDestroy(m->loaded[i]);
+            cudaEventDestroy(m->stepped[i]);
+            cudaEventDestroy(m->freed[i]);
+        }
+        for (int i = 0; i < kDoneRing; ++i) cudaEventDestroy(m->done[i]);
+        cudaStreamDestroy(m->pipe_in);
+        cudaStreamDestroy(m->pipe_out);
+        for (int f = 0; f < 5; ++f) cudaFree(m->pipe_fields[f]);
+    }
     cudaFree(m->scratch);
     cudaFree(m->st.psi1);
     cudaFree(m->st.v1);
@@ -226,35 +249,121 @@ int mpdata_step(mpdata_t *m, const void *h, void *psi, const void *u1, const voi
     return MPDATA_OK;
 }
 
-int mpdata_solve_host(mpdata_t *m, const void *h, void *psi, const void *u1, const void *u2,
-                      const void *u3, int nsteps, void *stream) {
-    if (!m) return fail(MPDATA_EINVAL, "handle is NULL");
-    const void *src[5] = {h, psi, u1, u2, u3};
+namespace {
+
+// Device copies of the five fields for a host solve (allocated once).
+int alloc_fields(mpdata_t *m, void **f) {
+    const size_t bytes = (size_t)m->n * m->esize;
+    for (int k = 0; k < 5; ++k) {
+        if (f[k]) continue;
+        cudaError_t e = cudaMalloc(&f[k], bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            f[k] = nullptr;
+            return fail(MPDATA_ENOMEM, "device allocation of %zu bytes failed", bytes);
+        }
+    }
+    return MPDATA_OK;
+}
+
+int check_host_args(const void *const src[5], int nsteps) {
     const char *names[5] = {"h", "psi", "u1", "u2", "u3"};
     for (int f = 0; f < 5; ++f)
         if (!src[f]) return fail(MPDATA_EINVAL, "%s is NULL", names[f]);
     if (nsteps < 0) return fail(MPDATA_EINVAL, "nsteps must be >= 0");
+    return MPDATA_OK;
+}
+
+int pipe_init(mpdata_t *m) {
+    cudaError_t e = cudaStreamCreateWithFlags(&m->pipe_in, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&m->pipe_out, cudaStreamNonBlocking);
+    for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
+        e = cudaEventCreateWithFlags(&m->loaded[i], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&m->stepped[i], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&m->freed[i], cudaEventDisableTiming);
+    }
+    for (int i = 0; i < kDoneRing && e == cudaSuccess; ++i)
+        e = cudaEventCreateWithFlags(&m->done[i], cudaEventDisableTiming);
+    if (e != cudaSuccess) return cuda_fail(e, "creating the host pipeline's streams and events");
+    m->pipe_ready = true;
+    return MPDATA_OK;
+}
+
+}  // namespace
+
+int mpdata_solve_host(mpdata_t *m, const void *h, void *psi, const void *u1, const void *u2,
+                      const void *u3, int nsteps, void *stream) {
+    if (!m) return fail(MPDATA_EINVAL, "handle is NULL");
+    const void *src[5] = {h, psi, u1, u2, u3};
+    int rc = check_host_args(src, nsteps);
+    if (rc) return rc;
+    if ((rc = alloc_fields(m, m->host_fields))) return rc;
     const size_t bytes = (size_t)m->n * m->esize;
     cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e;
+    // pipelined solves share slot 0 and the scratch buffer: wait for the last
+    // one to be copied out (every earlier one has been by then)
+    if (m->pipe_ready && m->issued && (e = cudaStreamWaitEvent(s, m->done[m->issued % kDoneRing], 0)) != cudaSuccess)
+        return cuda_fail(e, "cudaStreamWaitEvent");
     for (int f = 0; f < 5; ++f) {
-        if (!m->host_fields[f]) {
-            cudaError_t e = cudaMalloc(&m->host_fields[f], bytes);
-            if (e != cudaSuccess) {
-                cudaGetLastError();
-                m->host_fields[f] = nullptr;
-                return fail(MPDATA_ENOMEM, "device allocation of %zu bytes failed", bytes);
-            }
-        }
-        cudaError_t e = cudaMemcpyAsync(m->host_fields[f], src[f], bytes, cudaMemcpyHostToDevice, s);
+        e = cudaMemcpyAsync(m->host_fields[f], src[f], bytes, cudaMemcpyHostToDevice, s);
         if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync host to device");
     }
-    int rc = mpdata_step(m, m->host_fields[0], m->host_fields[1], m->host_fields[2],
-                         m->host_fields[3], m->host_fields[4], nsteps, stream);
+    rc = mpdata_step(m, m->host_fields[0], m->host_fields[1], m->host_fields[2],
+                     m->host_fields[3], m->host_fields[4], nsteps, stream);
     if (rc) return rc;
-    cudaError_t e = cudaMemcpyAsync(psi, m->host_fields[1], bytes, cudaMemcpyDeviceToHost, s);
+    e = cudaMemcpyAsync(psi, m->host_fields[1], bytes, cudaMemcpyDeviceToHost, s);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync device to host");
     e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    return MPDATA_OK;
+}
+
+int mpdata_host_submit(mpdata_t *m, const void *h, const void *psi_in, const void *u1,
+                       const void *u2, const void *u3, int nsteps, void *psi_out, void *stream,
+                       unsigned long long *ticket) {
+    if (!m) return fail(MPDATA_EINVAL, "handle is NULL");
+    if (!psi_out || !ticket) return fail(MPDATA_EINVAL, "psi_out or ticket is NULL");
+    const void *src[5] = {h, psi_in, u1, u2, u3};
+    int rc = check_host_args(src, nsteps);
+    if (rc) return rc;
+    if (!m->pipe_ready && (rc = pipe_init(m))) return rc;
+    const int sl = (int)(m->issued & 1);  // ticket issued + 1 takes slot issued % 2
+    void **f = sl ? m->pipe_fields : m->host_fields;
+    if ((rc = alloc_fields(m, f))) return rc;
+    const size_t bytes = (size_t)m->n * m->esize;
+    cudaStream_t s = (cudaStream_t)stream;
+    const unsigned long long t = m->issued + 1;
+    cudaError_t e = cudaSuccess;
+    // copy in once the slot's previous solve has been copied out
+    if (m->slot_used[sl]) e = cudaStreamWaitEvent(m->pipe_in, m->freed[sl], 0);
+    for (int k = 0; k < 5 && e == cudaSuccess; ++k)
+        e = cudaMemcpyAsync(f[k], src[k], bytes, cudaMemcpyHostToDevice, m->pipe_in);
+    if (e == cudaSuccess) e = cudaEventRecord(m->loaded[sl], m->pipe_in);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, m->loaded[sl], 0);
+    if (e != cudaSuccess) return cuda_fail(e, "enqueueing the copy in");
+    if ((rc = mpdata_step(m, f[0], f[1], f[2], f[3], f[4], nsteps, stream))) return rc;
+    e = cudaEventRecord(m->stepped[sl], s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(m->pipe_out, m->stepped[sl], 0);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(psi_out, f[1], bytes, cudaMemcpyDeviceToHost, m->pipe_out);
+    if (e == cudaSuccess) e = cudaEventRecord(m->freed[sl], m->pipe_out);
+    if (e == cudaSuccess) e = cudaEventRecord(m->done[t % kDoneRing], m->pipe_out);
+    if (e != cudaSuccess) return cuda_fail(e, "enqueueing the copy out");
+    m->slot_used[sl] = true;
+    m->issued = t;
+    *ticket = t;
+    return MPDATA_OK;
+}
+
+int mpdata_host_wait(mpdata_t *m, unsigned long long ticket) {
+    if (!m) return fail(MPDATA_EINVAL, "handle is NULL");
+    if (ticket == 0 || ticket > m->issued) return fail(MPDATA_ENOENT, "ticket %llu was not issued", ticket);
+    if (ticket <= m->waited) return MPDATA_OK;
+    // a ring entry re-recorded by a later ticket completes after this one
+    // (the copies out run in submit order), so the wait is never early
+    cudaError_t e = cudaEventSynchronize(m->done[ticket % kDoneRing]);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaEventSynchronize");
+    m->waited = ticket;
     return MPDATA_OK;
 }
 
