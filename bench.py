@@ -302,11 +302,16 @@ def run_tracers(args):
     stream = torch.cuda.current_stream()
     res = {}
 
-    def time_batch(idx, **kw):
-        """ms per bench step of a batch of the grids idx (graph replay)."""
+    def time_batch(idx, persistent=False, **kw):
+        """ms per bench step of a batch of the grids idx (graph replay); the
+        default split (one CTA per tile) or the balanced persistent one."""
         with mp.Batch([(fs[i].nx, fs[i].ny, fs[i].nz, fs[i].periodic) for i in idx], **kw) as b:
             for k, i in enumerate(idx):
                 b.set_fields(k, *ts[i])
+            if persistent:
+                for var in range(mp.Batch.VARIANTS):
+                    if b.work(var)[0]:
+                        b.set_balanced_split(var, nsm)
             for _ in range(args.warmup):
                 b.step(nsteps, graph=True)
             torch.cuda.synchronize()
@@ -318,8 +323,10 @@ def run_tracers(args):
             torch.cuda.synchronize()
             return e0.elapsed_time(e1) / args.steps
 
+    nsm = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
     every = list(range(len(fs)))
     res["batched"] = time_batch(every)
+    res["batched_persistent"] = time_batch(every, persistent=True)
     # per-grid tile shapes: per-shape rates measured on the whole batch, then
     # each grid's shape from the batch-level model
     from paper_1507_01265_gb300 import tune
@@ -330,7 +337,6 @@ def run_tracers(args):
         work = sum(math.ceil(fs[i].nx / 32) * math.ceil(fs[i].ny / ty) * 32 * ty * (fs[i].nz + 3)
                    for i in pairs)
         rates[ty] = work * nsteps / (ms * 1e-3)
-    nsm = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
     chosen = dict(zip(pairs, tune.choose_tiles([(fs[i].nx, fs[i].ny, fs[i].nz) for i in pairs], rates, nsm)))
     tiles = [chosen.get(i, 0) for i in every]
     res["per_grid_tiles"] = time_batch(every, tiles=tiles)
@@ -354,11 +360,13 @@ def run_tracers(args):
             "warmup": args.warmup, "ms_per_step": res["batched"], "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "64 tracer grids, nx/ny log-uniform [32,512], nz [16,64], 20 steps; "
-                                   "persistent batched launch captured in a CUDA graph",
+                                   "batched launch (one CTA per tile, largest first) captured in a CUDA graph",
                        "cells": cells, "mpdata_steps_per_step": nsteps},
             "per_grid_launches": {"value": cells * nsteps / (res["per_grid"] * 1e-3) / 1e9,
                                   "ms_per_step": res["per_grid"]},
             "speedup_vs_per_grid": res["per_grid"] / res["batched"],
+            "persistent_balanced_split": {"value": cells * nsteps / (res["batched_persistent"] * 1e-3) / 1e9,
+                                          "ms_per_step": res["batched_persistent"]},
             "per_grid_tiles": {"value": cells * nsteps / (res["per_grid_tiles"] * 1e-3) / 1e9,
                                "ms_per_step": res["per_grid_tiles"],
                                "grids": len(pairs),

@@ -218,16 +218,19 @@ int mpdata_courant_max(mpdata_t *handle, const void *h, const void *u1, const vo
 int mpdata_mass_noalloc(const void *h, const void *psi, long long n, int dtype, void *out3,
                         void *stream);
 
-/* ---- batches: many independent grids advanced by persistent launches ----
+/* ---- batches: many independent grids advanced by batched launches ----
  *
  * The paper's team decomposition (§5.3) assigns sub-domains to groups of
  * cores; here every grid of the batch is cut into the same tiles as a
- * single-grid launch, the tiles of all grids form a work-item list, and a
- * persistent launch of one CTA per SM runs the list with CTA c taking the
- * contiguous items [begin[c], begin[c+1]).  The default split balances the
- * estimated cost (tile area x (nz + 3)); mpdata_batch_set_split installs any
- * other, e.g. the uneven splits of the speed-function partitioner
- * (Algorithm 1, §4).  Each grid has its own tile shape (32x24, 32x16 or
+ * single-grid launch, the tiles of all grids form a work-item list ordered by
+ * decreasing estimated cost (tile area x (nz + 3)), and a launch runs the
+ * list with CTA c taking the contiguous items [begin[c], begin[c+1]).  The
+ * default split gives every item its own CTA (the hardware starts the largest
+ * tiles first and hands each free SM the next one).  mpdata_batch_set_split
+ * installs any other: the balanced persistent split (one CTA per SM,
+ * contiguous ranges of nearly equal cost) or the uneven splits of the
+ * speed-function partitioner (Algorithm 1, §4), whose processors are
+ * persistent CTAs.  Each grid has its own tile shape (32x24, 32x16 or
  * 32x28) and runs the two-column kernel: variant 0 (tile 32x24, x and y
  * periodic), 1 (32x24, a lid on x or y), 3 (32x16, periodic), 4 (32x16,
  * lid), 5 (32x28, periodic), 6 (32x28, lid); variant 2 is reserved and
@@ -258,7 +261,9 @@ int mpdata_batch_work(mpdata_batch_t *batch, int variant, int *nitems, int *ncta
 /* Copy the current split of a variant (ncta + 1 ints) into begin. */
 int mpdata_batch_get_split(mpdata_batch_t *batch, int variant, int *begin);
 /* Install a split: ncta CTAs, begin[0] = 0, begin[ncta] = nitems,
- * nondecreasing (a CTA may get no item). */
+ * nondecreasing (a CTA may get no item).  begin == NULL installs the balanced
+ * split over min(ncta, nitems) CTAs: CTA c's last item is the one whose
+ * cumulative cost is closest to (c+1)/ncta of the total. */
 int mpdata_batch_set_split(mpdata_batch_t *batch, int variant, int ncta, const int *begin);
 /* nsteps steps of every grid (async on stream).  use_graph != 0 captures the
  * whole sequence once per nsteps into a CUDA graph and replays it (the graph

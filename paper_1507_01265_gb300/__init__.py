@@ -182,9 +182,10 @@ class Solver:
 
 
 class Batch:
-    """Many independent FP32 grids advanced together by persistent launches
-    (mpdata_batch_*).  `grids` is a list of (nx, ny, nz) or (nx, ny, nz,
-    (px, py, pz)); fields are attached per grid with set_fields."""
+    """Many independent FP32 grids advanced together by batched launches
+    (mpdata_batch_*; one CTA per tile by default, largest tiles first).
+    `grids` is a list of (nx, ny, nz) or (nx, ny, nz, (px, py, pz)); fields
+    are attached per grid with set_fields."""
 
     # 0/1: two-column 32x24 (x/y periodic / a lid), 2: reserved (empty),
     # 3/4: two-column 32x16, 5/6: two-column 32x28
@@ -259,6 +260,12 @@ class Batch:
         begin = [int(v) for v in begin]
         buf = (ctypes.c_int * len(begin))(*begin)
         check(_lib.lib.mpdata_batch_set_split(self._h, int(variant), len(begin) - 1, buf),
+              "mpdata_batch_set_split")
+
+    def set_balanced_split(self, variant, ncta: int) -> None:
+        """Persistent split: min(ncta, items) CTAs, contiguous ranges of
+        nearly equal estimated cost (items are ordered largest first)."""
+        check(_lib.lib.mpdata_batch_set_split(self._h, int(variant), int(ncta), None),
               "mpdata_batch_set_split")
 
     def step(self, nsteps: int, graph: bool = False, stream=None) -> None:

@@ -1,17 +1,19 @@
-// Batched persistent launch of many independent grids (C ABI in
-// include/mpdata.h: mpdata_batch_*).
+// Batched launch of many independent grids (C ABI in include/mpdata.h:
+// mpdata_batch_*).
 //
 // Every grid is cut into the same tiles as a single-grid launch with its
-// tile shape (per grid: 32x24 or 32x16).  Tiles of all grids that use the
-// same kernel variant (kernel, tile shape, lid or not) form one work-item list
-// (grid, tile); a persistent launch of one CTA per SM runs the list, CTA c
-// taking the contiguous items [begin[c], begin[c+1]).  The default split
-// balances the estimated cost (tile area x (nz + 3) planes); callers (the
-// speed-function autotuner) may install any other split, including uneven
-// ones.  A step of the batch is one launch per variant; nsteps steps can be
-// captured once into a CUDA graph and replayed.  Each tile is computed by the
-// same code whichever CTA runs it, so every grid's result is bit-identical to
-// the single-grid launch.
+// tile shape (per grid: 32x24, 32x16 or 32x28).  Tiles of all grids that use
+// the same kernel variant (tile shape, lid or not) form one work-item list
+// (grid, tile), ordered by decreasing estimated cost (tile area x (nz + 3)
+// planes); a launch runs the list with CTA c taking the contiguous items
+// [begin[c], begin[c+1]).  The default split gives every item its own CTA,
+// so the hardware hands the largest tiles out first and every free SM takes
+// the next one; the balanced split (one CTA per SM, contiguous ranges of
+// nearly equal cost) and any other split, including the uneven ones of the
+// speed-function autotuner, can be installed instead.  A step of the batch is
+// one launch per variant; nsteps steps can be captured once into a CUDA graph
+// and replayed.  Each tile is computed by the same code whichever CTA runs
+// it, so every grid's result is bit-identical to the single-grid launch.
 #include <stdarg.h>
 #include <stdio.h>
 #include <string.h>
@@ -48,7 +50,8 @@ int variant_tile_y(int v) {
 bool variant_lid(int v) { return v == kPairs24Lid || v == kPairs16Lid || v == kPairs28Lid; }
 
 struct Group {
-    std::vector<int2> items;  // (grid, tile)
+    std::vector<int2> items;  // (grid, tile), by decreasing cost
+    std::vector<double> cost; // per item
     std::vector<int> begin;   // ncta + 1
     int2 *d_items = nullptr;
     int *d_begin = nullptr;
@@ -113,6 +116,14 @@ void balanced_split(const std::vector<double> &cost, int ncta, std::vector<int> 
 }
 
 double item_cost(const BatchGrid &g, int tx, int ty) { return (double)tx * ty * (g.g.nz + 3); }
+
+// One CTA per item (the default).
+void per_item_split(Group &G) {
+    const int n = (int)G.items.size();
+    G.ncta = n;
+    G.begin.resize(n + 1);
+    for (int i = 0; i <= n; ++i) G.begin[i] = i;
+}
 
 int upload_group(mpdata_batch *b, int v) {
     Group &G = b->group[v];
@@ -195,7 +206,6 @@ int mpdata_batch_create_tiles(int ngrids, const int *dims, const int *periodic, 
     b->variant.resize(ngrids);
     b->bytes.resize(ngrids);
     b->has_fields.assign(ngrids, false);
-    std::vector<std::vector<double>> costs(kNumVariants);
     for (int i = 0; i < ngrids; ++i) {
         const int nx = dims[3 * i], ny = dims[3 * i + 1], nz = dims[3 * i + 2];
         if (nx < 1 || ny < 1 || nz < 1 || ny > 65535 || nz > 65535 || (long long)nx * ny * nz >= (1LL << 31)) {
@@ -222,15 +232,23 @@ int mpdata_batch_create_tiles(int ngrids, const int *dims, const int *periodic, 
         b->bytes[i] = (size_t)nx * ny * nz * sizeof(float);
         for (int tl = 0; tl < ntiles; ++tl) {
             b->group[v].items.push_back(make_int2(i, tl));
-            costs[v].push_back(item_cost(g, tx, ty));
+            b->group[v].cost.push_back(item_cost(g, tx, ty));
         }
         e = cudaMalloc((void **)&g.buf[1], b->bytes[i]);  // scratch partner of psi
         if (e != cudaSuccess) { cudaGetLastError(); mpdata_batch_destroy(b); return bfail(MPDATA_ENOMEM, "scratch allocation for grid %d failed", i); }
     }
     for (int v = 0; v < kNumVariants; ++v) {
         Group &G = b->group[v];
-        G.ncta = G.items.empty() ? 0 : (int)std::min<size_t>(G.items.size(), (size_t)b->nsm);
-        if (G.ncta) balanced_split(costs[v], G.ncta, G.begin);
+        // largest items first (stable: a grid's tiles keep their order)
+        std::vector<int> order(G.items.size());
+        for (size_t k = 0; k < order.size(); ++k) order[k] = (int)k;
+        std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return G.cost[x] > G.cost[y]; });
+        std::vector<int2> items(order.size());
+        std::vector<double> cost(order.size());
+        for (size_t k = 0; k < order.size(); ++k) { items[k] = G.items[order[k]]; cost[k] = G.cost[order[k]]; }
+        G.items.swap(items);
+        G.cost.swap(cost);
+        per_item_split(G);
     }
     e = cudaMalloc((void **)&b->d_grids, sizeof(BatchGrid) * ngrids);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->capture_stream, cudaStreamNonBlocking);
@@ -279,9 +297,18 @@ int mpdata_batch_get_split(mpdata_batch_t *b, int variant, int *begin) {
 }
 
 int mpdata_batch_set_split(mpdata_batch_t *b, int variant, int ncta, const int *begin) {
-    if (!b || variant < 0 || variant >= kNumVariants || !begin) return bfail(MPDATA_EINVAL, "bad arguments");
+    if (!b || variant < 0 || variant >= kNumVariants) return bfail(MPDATA_EINVAL, "bad arguments");
     Group &G = b->group[variant];
     const int n = (int)G.items.size();
+    if (!begin) {  // the balanced split over ncta CTAs
+        if (ncta < 1) return bfail(MPDATA_EINVAL, "ncta must be >= 1");
+        if (n == 0) return MPDATA_OK;
+        G.ncta = std::min(ncta, n);
+        balanced_split(G.cost, G.ncta, G.begin);
+        G.dirty = true;
+        drop_graphs(b);
+        return MPDATA_OK;
+    }
     if (ncta < 1 || begin[0] != 0 || begin[ncta] != n)
         return bfail(MPDATA_EINVAL, "split must have ncta >= 1, begin[0] = 0, begin[ncta] = %d", n);
     for (int c = 0; c < ncta; ++c)

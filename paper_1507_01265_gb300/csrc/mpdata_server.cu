@@ -6,10 +6,11 @@
 //     footprint (h, psi, scratch, u1, u2, u3) fits the HBM budget and a slot is
 //     free; their fields are copied in on the stream;
 //   * tick: every resident request is advanced by the same chunk of steps
-//     (chunk = min(chunk_steps, fewest remaining)); each step is one persistent
-//     batched launch per kernel variant over the tiles of all resident
-//     requests (the same kernels and tiles as a single-grid step, so each
-//     result is bit-identical to running that request alone);
+//     (chunk = min(chunk_steps, fewest remaining)); each step is one batched
+//     launch per kernel variant over the tiles of all resident requests, one
+//     CTA per tile, largest tiles first (the same kernels and tiles as a
+//     single-grid step, so each result is bit-identical to running that
+//     request alone);
 //   * completion: a finished request's psi is copied back to its host buffer,
 //     its device memory is freed and its budget released once the copy is
 //     done; requests that arrive meanwhile join at the next tick.
@@ -161,20 +162,6 @@ int load_request(mpdata_server *s, Request *r, bool injected) {
     return MPDATA_OK;
 }
 
-void balanced_split(const std::vector<double> &cost, int ncta, std::vector<int> &begin) {
-    const int n = (int)cost.size();
-    std::vector<double> prefix(n + 1, 0.0);
-    for (int i = 0; i < n; ++i) prefix[i + 1] = prefix[i] + cost[i];
-    begin.assign(ncta + 1, 0);
-    for (int c = 1; c < ncta; ++c) {
-        const double target = prefix[n] * c / ncta;
-        int i = (int)(std::lower_bound(prefix.begin(), prefix.end(), target) - prefix.begin());
-        if (i > 0 && target - prefix[i - 1] < prefix[i] - target) --i;
-        begin[c] = std::max(begin[c - 1], std::min(i, n));
-    }
-    begin[ncta] = n;
-}
-
 // One tick over `act` (no lock held): upload the work list, launch `chunk`
 // steps, and for requests that finish (or are cancelled) queue the copy-out,
 // the frees and the completion event.  Returns a CUDA error or success.
@@ -207,15 +194,16 @@ cudaError_t run_tick(mpdata_server *s, const std::vector<Request *> &act, int ch
     int item_base = 0;
     for (int v = 0; v < kNumVariants; ++v) {
         voff[v] = (int)begin_all.size();
-        ncta[v] = items[v].empty() ? 0 : std::min((int)items[v].size(), s->nsm);
-        if (ncta[v]) {
-            std::vector<int> b;
-            balanced_split(cost[v], ncta[v], b);
-            for (int &x : b) x += item_base;
-            begin_all.insert(begin_all.end(), b.begin(), b.end());
+        const int n = (int)items[v].size();
+        ncta[v] = n;  // one CTA per tile
+        if (n) {
+            std::vector<int> order(n);
+            for (int k = 0; k < n; ++k) order[k] = k;
+            std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return cost[v][x] > cost[v][y]; });
+            for (int k = 0; k < n; ++k) T.h_items.push_back(items[v][order[k]]);
+            for (int k = 0; k <= n; ++k) begin_all.push_back(item_base + k);
         }
-        T.h_items.insert(T.h_items.end(), items[v].begin(), items[v].end());
-        item_base += (int)items[v].size();
+        item_base += n;
     }
     T.h_begin = begin_all;
     e = ensure(&T.d_grids, &T.cap_grids, (size_t)na, s->stream);

@@ -1,4 +1,4 @@
-"""Speed-function autotuner for the persistent batched launch (§5.4, §4).
+"""Speed-function autotuner for the batched launch (§5.4, §4).
 
 The paper builds speed functions of its core teams by timing every team at
 once on equal workloads (so contention is included, §5.4), then feeds them
@@ -13,13 +13,17 @@ to Algorithm 1 to pick a possibly uneven partition.  The GPU analogue here:
     k CTAs with x_right tiles and P - k with x_left, or the balanced split;
   * the speed functions of the available tile shapes are compared and the
     shape with the shortest predicted step is chosen;
+  * `tune_grid` also times the library's default split, one CTA per tile
+    handed out by the hardware (largest first), against the balanced and
+    the partitioner's persistent splits;
   * in a batch of uneven grids each grid may get its own shape
     (`choose_tiles`): a tile of shape ty costs 32*ty*(nz+3) cell-planes over
-    the per-CTA rate of that shape (measured whole-GPU rate / P); the tiles
-    of one shape form one persistent launch whose time is that of its
-    slowest CTA under the batch's default split, plus a launch.  Starting from the best
-    of the uniform choices and the per-grid cheapest shapes, grids switch
-    shape while the predicted batch time drops.
+    the per-SM rate of that shape (measured whole-GPU rate / P); the tiles
+    of one shape form one launch of one CTA per tile, whose time is that of
+    handing the tiles out largest first to the SM that frees first, plus a
+    launch.  Starting from the best of the uniform choices and the per-grid
+    cheapest shapes, grids switch shape while the predicted batch time
+    drops.
 
   * `tile_times` measures the step time of single-grid launches per tile
     shape (the data behind the library's default-tile model: waves of tiles
@@ -76,6 +80,7 @@ def speed_function(tile=(32, 24), xs=(1, 2, 3, 4, 5, 6, 7, 8), nz=64, steps=6):
         f, t = _device_fields(nx, ny, nz)
         with Batch([(nx, ny, nz, (1, 1, 0))], tile=tile) as b:
             b.set_fields(0, *t)
+            b.set_balanced_split(b.grid_variant(0), P)  # P persistent CTAs, x tiles each
             n, ncta = b.work(b.grid_variant(0))
             assert n == P * x and ncta == P
             dt = _time_batch(b, steps)
@@ -92,37 +97,29 @@ def split_for(n_items, ncta, k, xl, xr):
     return list(np.concatenate([[0], np.cumsum(sizes)]).astype(int))
 
 
-def split_time(costs, nsm):
-    """Time of one persistent launch over items of the given costs with the
-    batch's default split: min(n, nsm) CTAs, boundary c at the item boundary
-    closest to c/ncta of the total cost; the slowest CTA decides."""
-    n = len(costs)
-    if n == 0:
+def list_time(costs, nsm):
+    """Time of one launch of one CTA per item: items handed out largest
+    first, each to the SM that frees first."""
+    import heapq
+    if not costs:
         return 0.0
-    ncta = min(n, nsm)
-    prefix = np.concatenate([[0.0], np.cumsum(costs)])
-    begin = [0]
-    for c in range(1, ncta):
-        target = prefix[-1] * c / ncta
-        i = int(np.searchsorted(prefix, target, side="left"))
-        if i > 0 and target - prefix[i - 1] < prefix[i] - target:
-            i -= 1
-        begin.append(max(begin[-1], min(i, n)))
-    begin.append(n)
-    return max(prefix[begin[c + 1]] - prefix[begin[c]] for c in range(ncta))
+    free = [0.0] * min(nsm, len(costs))
+    for c in sorted(costs, reverse=True):
+        heapq.heapreplace(free, free[0] + c)
+    return max(free)
 
 
 def batch_time(dims, tiles, rates, nsm, launch_s=50e-6, tx=32):
-    """Predicted time of one batched step: one persistent launch per tile
-    shape in use (items in batch order, default split), a tile of shape ty
-    costing tx*ty*(nz+3) cell-planes at rates[ty] / nsm per CTA, plus
-    launch_s per launch (a persistent launch's fill and drain: a second
-    shape's launch measured about 60 us per step on the tracer batch)."""
+    """Predicted time of one batched step: one launch per tile shape in use
+    (the library's default split, one CTA per tile), a tile of shape ty
+    costing tx*ty*(nz+3) cell-planes at rates[ty] / nsm per SM, plus
+    launch_s per launch (a launch's fill and drain: a second shape's launch
+    measured about 60 us per step on the tracer batch)."""
     items = {}
     for (nx, ny, nz), ty in zip(dims, tiles):
         tile_s = tx * ty * (nz + 3) / (rates[ty] / nsm)
         items.setdefault(ty, []).extend([tile_s] * (math.ceil(nx / tx) * math.ceil(ny / ty)))
-    return sum(split_time(c, nsm) + launch_s for c in items.values())
+    return sum(list_time(c, nsm) + launch_s for c in items.values())
 
 
 def choose_tiles(dims, rates, nsm, launch_s=50e-6):
@@ -171,6 +168,8 @@ def tune_grid(nx, ny, nz, periodic=(1, 1, 0), steps=10, tiles=((32, 28), (32, 24
         with Batch([(nx, ny, nz, periodic)], tile=tile) as b:
             b.set_fields(0, *t)
             variant = b.grid_variant(0)
+            t_tile = _time_batch(b, steps)  # default: one CTA per tile
+            b.set_balanced_split(variant, P)
             n, ncta = b.work(variant)
             t_bal = _time_batch(b, steps)
             chosen = b.get_split(variant)
@@ -181,7 +180,8 @@ def tune_grid(nx, ny, nz, periodic=(1, 1, 0), steps=10, tiles=((32, 28), (32, 24
         rec = {"tiles": ntiles, "speed_x": xs.tolist(), "speed_cells_per_s": ss.tolist(),
                "condition2": bool(cond2), "condition2_sizes": [x_at, x_more],
                "k_right": k, "x_left": xl, "x_right": xr, "predicted_step_s": t_pred,
-               "balanced_step_s": t_bal, "tuned_step_s": t_tuned,
+               "balanced_step_s": t_bal, "tuned_step_s": t_tuned, "per_tile_step_s": t_tile,
+               "gcell_steps_per_s_per_tile": nx * ny * nz / t_tile / 1e9,
                "gcell_steps_per_s_balanced": nx * ny * nz / t_bal / 1e9,
                "gcell_steps_per_s_tuned": nx * ny * nz / t_tuned / 1e9}
         report["shapes"]["%dx%d" % tile] = rec

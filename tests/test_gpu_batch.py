@@ -1,6 +1,7 @@
-"""Batched persistent launches: every grid of a batch gives exactly (bit for
-bit) what mpdata_step gives on that grid alone, whatever the mix of grids,
-the work split between CTAs, odd or even step counts, or graph replay."""
+"""Batched launches: every grid of a batch gives exactly (bit for bit) what
+mpdata_step gives on that grid alone, whatever the mix of grids, the work
+split between CTAs (one CTA per tile by default, balanced persistent, uneven),
+odd or even step counts, or graph replay."""
 import numpy as np
 import pytest
 
@@ -73,6 +74,42 @@ def test_uneven_and_degenerate_splits(mp):
         torch.cuda.synchronize()
     for f, t in zip(fs, ts):
         assert np.array_equal(t[1].double().cpu().numpy(), run_gpu(f, 3, tile=(32, 16))), f.name
+
+
+@pytest.mark.parametrize("graph", [False, True])
+def test_default_and_balanced_splits(mp, graph):
+    """The default split gives every work item its own CTA; the balanced
+    persistent split runs min(ncta, items) CTAs over contiguous ranges.  Both
+    give every grid the bits of its run alone."""
+    import torch
+    fs = [F.tracer_grid(nx, ny, nz, c, seed=90 + i, nsteps=3)
+          for i, (nx, ny, nz, c) in enumerate(F.tracer_batch_dims(count=10, seed=78))]
+    results = []
+    for balanced in (False, True):
+        ts = _fields(mp, fs)
+        with _batch(mp, fs) as b:
+            for i, t in enumerate(ts):
+                b.set_fields(i, *t)
+            for v in range(mp.Batch.VARIANTS):
+                n, ncta = b.work(v)
+                if n == 0:
+                    assert ncta == 0
+                    continue
+                assert ncta == n and b.get_split(v) == list(range(n + 1))
+                if balanced:
+                    b.set_balanced_split(v, 5)
+                    n2, ncta2 = b.work(v)
+                    split = b.get_split(v)
+                    assert n2 == n and ncta2 == min(5, n) and len(split) == ncta2 + 1
+                    assert split[0] == 0 and split[-1] == n and all(a <= c for a, c in zip(split, split[1:]))
+                    with pytest.raises(mp.MpdataError):
+                        b.set_balanced_split(v, 0)
+            b.step(3, graph=graph)
+            torch.cuda.synchronize()
+        results.append([t[1].double().cpu().numpy() for t in ts])
+    for f, a, c in zip(fs, *results):
+        alone = run_gpu(f, 3, tile=(32, 24))
+        assert np.array_equal(a, alone) and np.array_equal(c, alone), f.name
 
 
 def test_bad_split_is_rejected(mp):
