@@ -87,7 +87,7 @@ double now_s(Clock::time_point t0) {
 
 struct mpdata_server {
     mpdata_server_opts o;
-    int device = 0, nsm = 0;
+    int device = 0;
     cudaStream_t stream = nullptr;
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
@@ -397,7 +397,6 @@ int mpdata_server_create(const mpdata_server_opts *opts, mpdata_server_t **out) 
     if (!s) return sfail(MPDATA_ENOMEM, "host allocation failed");
     s->o = o;
     cudaError_t e = cudaGetDevice(&s->device);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&s->nsm, cudaDevAttrMultiProcessorCount, s->device);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
     for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&s->tick[i].ev, cudaEventDisableTiming);
     if (e != cudaSuccess) {
