@@ -114,7 +114,8 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
-FUSED_SOURCES = ("mpdata_fused2.cu", "mpdata_internal.cuh")  # the two-column kernel's code
+# the fused FP32 kernels and the tile / row-band planner that picks them
+FUSED_SOURCES = ("mpdata_fused2.cu", "mpdata_internal.cuh", "mpdata_fused.cu")
 
 
 def _code_only(text):
@@ -135,8 +136,9 @@ def fused_source_sha256():
 
 
 def kernel_record():
-    """The committed ncu record of the fused kernel (DRAM bytes and warp
-    instructions per cell), or None once the kernel code has changed."""
+    """The committed ncu record of one MPDATA step of the bench grid (DRAM
+    bytes and warp instructions per cell over the step's launches), or None
+    once the kernel or planner code has changed."""
     path = os.path.join(ROOT, "profiles", "fused_traffic.json")
     try:
         with open(path) as f:
@@ -147,7 +149,7 @@ def kernel_record():
 
 
 def kernel_traffic(ncells):
-    """DRAM bytes per launch of the fused kernel from the committed ncu
+    """DRAM bytes per MPDATA step of the fused kernels from the committed ncu
     summary, valid only while the kernel sources are unchanged."""
     rec = kernel_record()
     return None if rec is None else float(rec["bytes_per_cell"]) * ncells
@@ -644,18 +646,28 @@ def main():
     ms = max_over_ranks(evs[0].elapsed_time(evs[-1]), dist, dev)
     ms_per_step = ms / args.steps
     per_solve = [evs[i].elapsed_time(evs[i + 1]) for i in range(args.steps)]
-    launches = args.steps * NSTEPS
+    mpdata_steps = args.steps * NSTEPS
+    bands = solver.bands if args.path == "fused" else (0, 0)
+    launches = mpdata_steps * (2 if bands[0] else 1)
     value = world * ncells * NSTEPS * args.steps / (ms * 1e-3) / 1e9
 
-    # roofline of the fused kernel: the timed region holds only its launches
+    # roofline of one MPDATA step: the timed region holds only its launches
+    # (with row bands, two concurrent launches per step)
     peak, peak_kind = measured_peaks()
     algo_bytes = FIELDS * 4 * ncells
-    launch_s = ms * 1e-3 / launches
+    launch_s = ms * 1e-3 / mpdata_steps
     achieved = algo_bytes / launch_s / 1e9
+    if args.path != "fused":
+        kname = "stage kernels"
+    elif bands[0]:
+        kname = ("k_fused_pairs<32,28> (rows 0..%d) + k_fused_ws (32x24, rows %d..), concurrent"
+                 % (28 * bands[0] - 1, 28 * bands[0]))
+    else:
+        kname = "k_fused_pairs"
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": kernel_traffic(ncells),
-                "peak_kind": peak_kind, "kernel": "k_fused" if args.path == "fused" else "stage kernels",
-                "algorithmic_bytes_per_launch": algo_bytes}
+                "peak_kind": peak_kind, "kernel": kname,
+                "algorithmic_bytes_per_step": algo_bytes}
     rec = kernel_record() if args.path == "fused" else None
     if rec is not None and "warp_inst_per_cell" in rec:
         # what binds the kernel: instruction issue (one warp instruction per
@@ -703,7 +715,7 @@ def main():
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": dict(workload_config(), path=args.path, tile=list(solver.tile),
+            "config": dict(workload_config(), path=args.path, tile=list(solver.tile), bands=list(bands),
                            l2="inputs 671 MB + output 134 MB per launch > 129 MB L2 (no flush)",
                            parallelism="replicas" if world > 1 else "single"),
             "roofline": roofline, "e2e": e2e, "cpu_baseline": cpu,

@@ -103,6 +103,8 @@ void mpdata_opts_default(mpdata_opts *opts);
  * of 4 or 8 bytes per cell).  The handle owns one psi-sized device scratch buffer (the step's
  * ping-pong partner) and, for the stage-per-kernel path, the intermediate
  * arrays; they are allocated here and freed by mpdata_destroy.
+ * With tile_x = tile_y = 0 a large FP32 grid may run in row bands of two
+ * tile heights (mpdata_get_bands).
  * The fused path implements iterations 1 and 2 with the default extrema set
  * and pure precision; iterations = 3, MPDATA_EXTREMA_CORRECTED and
  * MPDATA_PREC_F64_BETA (with MPDATA_F32) need path = MPDATA_PATH_STAGES.
@@ -116,6 +118,17 @@ int mpdata_destroy(mpdata_t *handle);
  * opts.tile_x = tile_y = 0), written to *tile_x and *tile_y; 0 x 0 for the
  * stage path.  Errors: EINVAL (NULL argument). */
 int mpdata_get_tile(const mpdata_t *handle, int *tile_x, int *tile_y);
+
+/* Row bands of a default-tile handle (FP32, fused, iterations 2, x and y
+ * periodic, nx % 4 == 0, when the tile model predicts them faster): each step
+ * runs rows [0, 28 * n28) in 32x28 tiles and the rest in n24 bands of 32x24
+ * tiles (the last may end past ny), as two launches that run concurrently
+ * (a stream and two events owned by the handle fork from and join back into
+ * the caller's stream), so the SMs take tiles of both heights and no band is
+ * left mostly empty.  Results are bit-identical to a single tile shape.
+ * *n28 = *n24 = 0 when the handle runs one tile shape (mpdata_get_tile).
+ * Errors: EINVAL (NULL argument). */
+int mpdata_get_bands(const mpdata_t *handle, int *n28, int *n24);
 
 /* Advance psi by nsteps MPDATA steps in place (async on `stream`): each
  * step reads the five fields and writes psi (§5.2); a run is a loop of such

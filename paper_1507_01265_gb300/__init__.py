@@ -135,6 +135,14 @@ class Solver:
             del self._inflight[k]
 
     @property
+    def bands(self):
+        """(n28, n24): rows in n28 bands of 32x28 tiles, then n24 bands of
+        32x24 tiles, run concurrently; (0, 0) when one tile shape runs."""
+        a, b = ctypes.c_int(), ctypes.c_int()
+        check(_lib.lib.mpdata_get_bands(self._h, ctypes.byref(a), ctypes.byref(b)), "mpdata_get_bands")
+        return (a.value, b.value)
+
+    @property
     def tile(self):
         """(tile_x, tile_y) of the fused kernel this solver runs; (0, 0) on the stage path."""
         tx, ty = ctypes.c_int(), ctypes.c_int()

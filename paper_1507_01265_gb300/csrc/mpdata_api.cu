@@ -20,6 +20,10 @@ struct mpdata_handle {
     mpdata_opts opts;
     Grid grid;
     int tile_x, tile_y;
+    bool banded;              // default tile: rows in 32x28 and 32x24 bands (launch_fused_bands)
+    mpdata::BandPlan band;
+    cudaStream_t band_stream;  // the 32x24 bands' launches
+    cudaEvent_t band_fork, band_join;
     void *scratch;            // psi-sized ping-pong partner
     mpdata::StageBuffers st;  // stage-per-kernel intermediates (path STAGES only)
     double *partials;         // mass reduction partials (kReduceBlocks x 3)
@@ -89,6 +93,12 @@ constexpr int kDoneRing = 16;
 
 void free_handle(mpdata_t *m) {
     if (!m) return;
+    if (m->banded) {
+        if (m->band_join) cudaEventSynchronize(m->band_join);
+        if (m->band_fork) cudaEventDestroy(m->band_fork);
+        if (m->band_join) cudaEventDestroy(m->band_join);
+        if (m->band_stream) cudaStreamDestroy(m->band_stream);
+    }
     if (m->pipe_ready) {
         // the last copy out ends after every pipelined copy and step
         if (m->issued) cudaEventSynchronize(m->done[m->issued % kDoneRing]);
@@ -127,6 +137,9 @@ int launch_one(mpdata_t *m, const void *h, const void *src, const void *u1, cons
     else if (o.path == MPDATA_PATH_STAGES)
         e = mpdata::launch_stage_step(o.dtype, m->grid, o.iterations, o.nonoscillatory, o.extrema,
                                       o.precision, o.eps, h, src, u1, u2, u3, dst, m->st, s);
+    else if (m->banded)
+        e = mpdata::launch_fused_bands(m->grid, o.nonoscillatory, o.eps, m->band, h, src, u1, u2, u3, dst, s,
+                                       m->band_stream, m->band_fork, m->band_join);
     else
         e = mpdata::launch_fused_step(o.dtype, m->grid, o.nonoscillatory, o.eps, m->tile_x,
                                       m->tile_y, h, src, u1, u2, u3, dst, s);
@@ -169,6 +182,8 @@ int mpdata_create(int nx, int ny, int nz, const mpdata_opts *opts, mpdata_t **ou
     grid.nx = nx; grid.ny = ny; grid.nz = nz;
     for (int d = 0; d < 3; ++d) grid.per[d] = o.periodic[d];
     int tx = o.tile_x, ty = o.tile_y;
+    mpdata::BandPlan band{0, 0};
+    bool banded = false;
     if (tx == 0 && ty == 0) {
         int dev = 0, nsm = 0;
         if (cudaGetDevice(&dev) != cudaSuccess ||
@@ -177,6 +192,9 @@ int mpdata_create(int nx, int ny, int nz, const mpdata_opts *opts, mpdata_t **ou
             nsm = 0;  // no device yet: the SM count only tunes the default tile
         }
         mpdata::fused_default_tile(o.dtype, grid, nsm, &tx, &ty);
+        // a large FP32 grid may run as rows in 28- and 24-row bands instead
+        banded = o.dtype == MPDATA_F32 && o.path == MPDATA_PATH_FUSED && o.iterations == 2 && tx == 32 &&
+                 (ty == 24 || ty == 28) && mpdata::fused_band_plan(grid, nsm, &band);
     }
     if (o.path == MPDATA_PATH_FUSED && o.iterations == 2 && !mpdata::fused_tile_supported(o.dtype, grid, tx, ty))
         return fail(MPDATA_EINVAL, "no fused kernel for tile %d x %d on this grid", tx, ty);
@@ -200,6 +218,13 @@ int mpdata_create(int nx, int ny, int nz, const mpdata_opts *opts, mpdata_t **ou
             for (int i = 0; i < 4 && e == cudaSuccess; ++i) e = cudaMalloc(b3[i], bytes);
         }
     }
+    if (e == cudaSuccess && banded) {
+        m->banded = true;
+        m->band = band;
+        e = cudaStreamCreateWithFlags(&m->band_stream, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&m->band_fork, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&m->band_join, cudaEventDisableTiming);
+    }
     if (e != cudaSuccess) {
         cudaGetLastError();
         free_handle(m);
@@ -220,6 +245,13 @@ int mpdata_get_tile(const mpdata_t *m, int *tile_x, int *tile_y) {
     const bool fused = m->opts.path == MPDATA_PATH_FUSED && m->opts.iterations == 2;
     *tile_x = fused ? m->tile_x : 0;
     *tile_y = fused ? m->tile_y : 0;
+    return MPDATA_OK;
+}
+
+int mpdata_get_bands(const mpdata_t *m, int *n28, int *n24) {
+    if (!m || !n28 || !n24) return fail(MPDATA_EINVAL, "NULL argument");
+    *n28 = m->banded ? m->band.n28 : 0;
+    *n24 = m->banded ? m->band.n24 : 0;
     return MPDATA_OK;
 }
 

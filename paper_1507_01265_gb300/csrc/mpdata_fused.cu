@@ -27,6 +27,9 @@
 // Arithmetic: FP32 divisions are a hardware reciprocal (rcp.approx, <= 1 ulp)
 // times the numerator, one reciprocal per denominator; FP64 keeps IEEE
 // reciprocals.  Local extrema use the 3-input min/max of sm_100+.
+#include <algorithm>
+#include <map>
+
 #include "mpdata_internal.cuh"
 
 namespace mpdata {
@@ -453,6 +456,57 @@ void fused_default_tile(int dtype, const Grid &g, int nsm, int *tx, int *ty) {
         const double t = (double)((tiles + sms - 1) / sms) * (ws ? c.us_ws : aligned ? c.us_aligned : c.us_any);
         if (best == 0.0 || t < best * 0.98) { best = t; *tx = c.tx; *ty = c.ty; }
     }
+}
+
+namespace {
+
+// Finish time of nA tiles of cost tA and then nB of cost tB handed out, each
+// to the SM that frees first (the hardware starts the first launch's CTAs
+// first).  SM loads take few distinct values, so they are kept as levels.
+double handout_time(long long nA, double tA, long long nB, double tB, int nsm) {
+    std::map<double, long long> lv;
+    lv[0.0] = nsm;
+    auto assign = [&](long long n, double t) {
+        while (n > 0) {
+            auto it = lv.begin();
+            const double L = it->first;
+            const long long c = it->second, k = std::min(c, n);
+            if (k == c) lv.erase(it);
+            else it->second -= k;
+            lv[L + t] += k;
+            n -= k;
+        }
+    };
+    assign(nA, tA);
+    assign(nB, tB);
+    return lv.rbegin()->first;
+}
+
+}  // namespace
+
+bool fused_band_plan(const Grid &g, int nsm, BandPlan *plan) {
+    // Rows in 28-row bands of 32x28 tiles and 24-row bands of 32x24 tiles
+    // (warp-specialised), run concurrently: SMs that finish early take the
+    // next tile of either height, and the 24-row bands can end near ny where
+    // one tile height would leave a mostly empty band.  Per-plane times as in
+    // fused_default_tile; 0.1 x the 28-row plane time covers the fork and the
+    // join (measured on 1024x512: predicted 8.96 us-planes, measured 8.95).
+    const double t28 = 2.28, t24 = 1.89;
+    if (nsm <= 0 || g.nx % 4 != 0 || !g.per[0] || !g.per[1]) return false;
+    const long long ntx = (g.nx + 31) / 32;
+    const long long w24 = (ntx * ((g.ny + 23) / 24) + nsm - 1) / nsm, w28 = (ntx * ((g.ny + 27) / 28) + nsm - 1) / nsm;
+    const double single = std::min(w24 * t24, w28 * t28);
+    double best = 0.0;
+    for (int n28 = 1; 28 * n28 < g.ny; ++n28) {
+        const int n24 = (g.ny - 28 * n28 + 23) / 24;
+        const double t = handout_time(ntx * n28, t28, ntx * n24, t24, nsm) + 0.1 * t28;
+        if (best == 0.0 || t < best) {
+            best = t;
+            plan->n28 = n28;
+            plan->n24 = n24;
+        }
+    }
+    return best > 0.0 && best < 0.99 * single;
 }
 
 cudaError_t launch_fused_step(int dtype, const Grid &g, int nonosc, double eps, int tx, int ty,

@@ -214,7 +214,7 @@ __device__ __forceinline__ void pairs_tile(const TileArgs &a, int tile, float *s
     const int nx = g.nx, ny = g.ny, nz = g.nz;
     const int perx = LID ? g.per[0] : 1, pery = LID ? g.per[1] : 1, perz = g.per[2];
     const long long nxy = (long long)nx * ny;
-    const int x0 = (tile % ntx) * TX, y0 = (tile / ntx) * TY;
+    const int x0 = (tile % ntx) * TX, y0 = a.y0 + (tile / ntx) * TY;
     const F2 eps = bc(eps1);
 
     int px, ry;
@@ -562,7 +562,7 @@ __device__ __forceinline__ void ws_tile(const TileArgs &a, int tile, float *sm) 
     const int nx = g.nx, ny = g.ny, nz = g.nz;
     const int perz = g.per[2];
     const long long nxy = (long long)nx * ny;
-    const int x0 = (tile % ntx) * TX, y0 = (tile / ntx) * TY;
+    const int x0 = (tile % ntx) * TX, y0 = a.y0 + (tile / ntx) * TY;
     const F2 eps = bc(eps1);
     const int p_first = perz ? -3 : -1;
     const int p_last = nz + 2;
@@ -864,6 +864,7 @@ cudaError_t launch_pairs(const Grid &g, int nonosc, double eps, const void *h, c
     TileArgs a;
     a.g = g;
     a.ntx = ntx;
+    a.y0 = 0;
     a.eps = (float)eps;
     a.h = (const float *)h; a.psi = (const float *)psi; a.u1 = (const float *)u1;
     a.u2 = (const float *)u2; a.u3 = (const float *)u3; a.out = (float *)out;
@@ -910,6 +911,39 @@ cudaError_t launch_fused_pairs(const Grid &g, int nonosc, double eps, int tx, in
     if (tx == 32 && ty == 24) return launch_pairs<32, 24>(g, nonosc, eps, h, psi, u1, u2, u3, out, s);
     if (tx == 32 && ty == 28) return launch_pairs<32, 28>(g, nonosc, eps, h, psi, u1, u2, u3, out, s);
     return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_fused_bands(const Grid &g, int nonosc, double eps, const BandPlan &plan, const void *h,
+                               const void *psi, const void *u1, const void *u2, const void *u3,
+                               void *out, cudaStream_t s, cudaStream_t s2, cudaEvent_t ev_fork,
+                               cudaEvent_t ev_join) {
+    using L28 = Lay2<32, 28>;
+    using L24 = Lay2<32, 24>;
+    if (g.nx % 4 != 0 || !g.per[0] || !g.per[1] || plan.n28 < 1 || plan.n24 < 1) return cudaErrorInvalidValue;
+    auto k28 = nonosc ? k_fused_pairs<32, 28, true, false, 1> : k_fused_pairs<32, 28, false, false, 1>;
+    auto k24 = nonosc ? k_fused_ws<true> : k_fused_ws<false>;
+    const size_t sm28 = (size_t)L28::NPLANES * L28::PL * sizeof(float);
+    const size_t sm24 = (size_t)39 * L24::PL * sizeof(float);
+    cudaError_t e = cudaFuncSetAttribute(k28, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm28);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k24, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm24);
+    if (e == cudaSuccess) e = cudaEventRecord(ev_fork, s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s2, ev_fork, 0);
+    if (e != cudaSuccess) return e;
+    TileArgs a;
+    a.g = g;
+    a.ntx = (g.nx + 31) / 32;
+    a.eps = (float)eps;
+    a.h = (const float *)h; a.psi = (const float *)psi; a.u1 = (const float *)u1;
+    a.u2 = (const float *)u2; a.u3 = (const float *)u3; a.out = (float *)out;
+    a.y0 = 0;
+    k28<<<a.ntx * plan.n28, L28::NT, sm28, s>>>(a);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    a.y0 = 28 * plan.n28;
+    k24<<<a.ntx * plan.n24, 640, sm24, s2>>>(a);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    e = cudaEventRecord(ev_join, s2);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ev_join, 0);
+    return e;
 }
 
 cudaError_t launch_fused_pairs_batch(int tx, int ty, int nonosc, int lid, const BatchGrid *grids,

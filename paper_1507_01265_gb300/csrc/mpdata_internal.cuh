@@ -35,6 +35,7 @@ __device__ __forceinline__ T upstream_flux(T U, T L, T R) {
 struct TileArgs {
     Grid g;
     int ntx;  // tiles per row of this grid
+    int y0;   // grid row of tile row 0 (a band of rows; 0 for the whole grid)
     float eps;
     const float *h, *psi, *u1, *u2, *u3;
     float *out;
@@ -54,6 +55,7 @@ __host__ __device__ inline TileArgs batch_args(const BatchGrid &b, int parity) {
     TileArgs a;
     a.g = b.g;
     a.ntx = b.ntx;
+    a.y0 = 0;
     a.eps = b.eps;
     a.h = b.h; a.u1 = b.u1; a.u2 = b.u2; a.u3 = b.u3;
     a.psi = b.buf[parity];
@@ -93,6 +95,20 @@ cudaError_t launch_fused_pairs_batch(int tile_x, int tile_y, int nonosc, int lid
 cudaError_t launch_fused_pairs(const Grid &g, int nonosc, double eps, int tile_x, int tile_y,
                                const void *h, const void *psi, const void *u1, const void *u2,
                                const void *u3, void *out, cudaStream_t s);
+// Row bands of an FP32 grid (x and y periodic, nx % 4 == 0): rows [0, 28 n28)
+// in 32x28 tiles and [28 n28, ny) in 32x24 tiles (the last band may end past
+// ny), launched concurrently on s and s2 (fork and join through the events)
+// so that the hardware mixes the two tile sizes over the SMs.
+struct BandPlan {
+    int n28, n24;
+};
+// True when the default-tile model predicts the bands faster than the best
+// single pair tile (waves x per-plane time) by at least 1 %.
+bool fused_band_plan(const Grid &g, int nsm, BandPlan *plan);
+cudaError_t launch_fused_bands(const Grid &g, int nonosc, double eps, const BandPlan &plan, const void *h,
+                               const void *psi, const void *u1, const void *u2, const void *u3,
+                               void *out, cudaStream_t s, cudaStream_t s2, cudaEvent_t ev_fork,
+                               cudaEvent_t ev_join);
 
 // Record the calling thread's last error message (mpdata_api.cu); returns code.
 int set_error(int code, const char *message);

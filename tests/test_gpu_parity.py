@@ -364,6 +364,27 @@ def test_default_tile_choice():
 
 
 @pytest.mark.parametrize("nonosc", [True, False])
+@pytest.mark.parametrize("nx,ny,nz,bands", [(1024, 512, 4, (14, 5)), (2048, 1024, 2, (4, 38))])
+def test_row_bands(nx, ny, nz, bands, nonosc):
+    """With the default tile a large x/y-periodic grid runs in rows of 32x28
+    and 32x24 bands, two concurrent launches per step.  Every cell is computed
+    by the same arithmetic as with one tile shape: the banded result equals
+    both single-shape results bit for bit."""
+    import torch
+    import paper_1507_01265_gb300 as mp
+    if torch.cuda.get_device_properties(0).multi_processor_count != 152:
+        pytest.skip("band plans are tuned for 152 SMs")
+    f = rand_problem((nz, ny, nx), seed=ny + nz, periodic=(1, 1, 0))
+    with mp.Solver(nx, ny, nz, periodic=(1, 1, 0)) as s:
+        assert s.bands == bands
+    banded = run_gpu(f, 3, nonosc=nonosc)
+    for tile in ((32, 28), (32, 24)):
+        with mp.Solver(nx, ny, nz, periodic=(1, 1, 0), tile=tile) as s:
+            assert s.bands == (0, 0)
+        assert np.array_equal(banded, run_gpu(f, 3, tile=tile, nonosc=nonosc)), tile
+
+
+@pytest.mark.parametrize("nonosc", [True, False])
 @pytest.mark.parametrize("nx,ny,nz,per", [
     (96, 50, 9, (1, 1, 0)), (128, 61, 7, (1, 1, 1)), (64, 24, 33, (1, 1, 0)), (32, 5, 4, (1, 1, 1)),
 ])
