@@ -489,8 +489,9 @@ bool fused_band_plan(const Grid &g, int nsm, BandPlan *plan) {
     // (warp-specialised), run concurrently: SMs that finish early take the
     // next tile of either height, and the 24-row bands can end near ny where
     // one tile height would leave a mostly empty band.  Per-plane times as in
-    // fused_default_tile; 0.1 x the 28-row plane time covers the fork and the
-    // join (measured on 1024x512: predicted 8.96 us-planes, measured 8.95).
+    // fused_default_tile; 0.02 x the 28-row plane time covers the fork and the
+    // join (1024x512: predicted 8.78 us-planes, measured 8.71, i.e. 53.97
+    // against 51.57 Gcell-steps/s for 32x28 alone).
     const double t28 = 2.28, t24 = 1.89;
     if (nsm <= 0 || g.nx % 4 != 0 || !g.per[0] || !g.per[1]) return false;
     const long long ntx = (g.nx + 31) / 32;
@@ -499,7 +500,7 @@ bool fused_band_plan(const Grid &g, int nsm, BandPlan *plan) {
     double best = 0.0;
     for (int n28 = 1; 28 * n28 < g.ny; ++n28) {
         const int n24 = (g.ny - 28 * n28 + 23) / 24;
-        const double t = handout_time(ntx * n28, t28, ntx * n24, t24, nsm) + 0.1 * t28;
+        const double t = handout_time(ntx * n28, t28, ntx * n24, t24, nsm) + 0.02 * t28;
         if (best == 0.0 || t < best) {
             best = t;
             plan->n28 = n28;
