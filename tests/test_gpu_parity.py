@@ -384,6 +384,35 @@ def test_row_bands(nx, ny, nz, bands, nonosc):
         assert np.array_equal(banded, run_gpu(f, 3, tile=tile, nonosc=nonosc)), tile
 
 
+def test_row_bands_in_a_cuda_graph():
+    """A banded step forks onto the handle's stream and joins back; captured
+    into a CUDA graph by the caller it replays to the eager result."""
+    import torch
+    import paper_1507_01265_gb300 as mp
+    if torch.cuda.get_device_properties(0).multi_processor_count != 152:
+        pytest.skip("band plans are tuned for 152 SMs")
+    nx, ny, nz = 1024, 512, 3
+    f = rand_problem((nz, ny, nx), seed=5, periodic=(1, 1, 0))
+    eager = run_gpu(f, 4)
+    t = [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in (f.h, f.psi, f.u1, f.u2, f.u3)]
+    with mp.Solver(nx, ny, nz, periodic=(1, 1, 0)) as s:
+        assert s.bands != (0, 0)
+        g = torch.cuda.CUDAGraph()
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            s.step(*t, 2, stream=side)  # warm up outside the capture (kernel attributes)
+        torch.cuda.current_stream().wait_stream(side)
+        torch.cuda.synchronize()
+        t[1].copy_(torch.from_numpy(np.ascontiguousarray(f.psi)))
+        with torch.cuda.graph(g):
+            s.step(*t, 2, stream=torch.cuda.current_stream())
+        g.replay()
+        g.replay()
+        torch.cuda.synchronize()
+    assert np.array_equal(t[1].double().cpu().numpy(), eager)
+
+
 @pytest.mark.parametrize("nonosc", [True, False])
 @pytest.mark.parametrize("nx,ny,nz,per", [
     (96, 50, 9, (1, 1, 0)), (128, 61, 7, (1, 1, 1)), (64, 24, 33, (1, 1, 0)), (32, 5, 4, (1, 1, 1)),
