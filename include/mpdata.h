@@ -130,6 +130,13 @@ int mpdata_get_tile(const mpdata_t *handle, int *tile_x, int *tile_y);
  * Errors: EINVAL (NULL argument). */
 int mpdata_get_bands(const mpdata_t *handle, int *n28, int *n24);
 
+/* The row-band plan mpdata_create would take for an FP32 nx x ny x nz grid
+ * with the default tile on a device of nsm SMs (host only, no device call):
+ * *n28, *n24 as in mpdata_get_bands, 0 and 0 for one tile shape.  Plans are
+ * considered for x/y-periodic grids with nx % 4 == 0 and at most 48 waves of
+ * tiles.  Errors: EINVAL (NULL argument, dims < 1, nsm < 0). */
+int mpdata_plan_bands(int nx, int ny, int nz, const int *periodic, int nsm, int *n28, int *n24);
+
 /* Advance psi by nsteps MPDATA steps in place (async on `stream`): each
  * step reads the five fields and writes psi (§5.2); a run is a loop of such
  * steps (§6 times 40 of them).

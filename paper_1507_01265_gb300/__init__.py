@@ -33,6 +33,16 @@ def _stream_handle(stream):
     return ctypes.c_void_p(stream.cuda_stream)
 
 
+def plan_bands(nx: int, ny: int, nz: int, periodic=(1, 1, 0), nsm: int = 152):
+    """(n28, n24): the row bands a default-tile FP32 solver of this grid runs
+    on a device of nsm SMs ((0, 0): one tile shape).  Host only."""
+    per = (ctypes.c_int * 3)(*[int(p) for p in periodic])
+    a, b = ctypes.c_int(), ctypes.c_int()
+    check(_lib.lib.mpdata_plan_bands(int(nx), int(ny), int(nz), per, int(nsm), ctypes.byref(a), ctypes.byref(b)),
+          "mpdata_plan_bands")
+    return (a.value, b.value)
+
+
 class Solver:
     """One MPDATA problem size and option set (wraps an mpdata_t handle)."""
 

@@ -248,6 +248,19 @@ int mpdata_get_tile(const mpdata_t *m, int *tile_x, int *tile_y) {
     return MPDATA_OK;
 }
 
+int mpdata_plan_bands(int nx, int ny, int nz, const int *periodic, int nsm, int *n28, int *n24) {
+    if (!periodic || !n28 || !n24) return fail(MPDATA_EINVAL, "NULL argument");
+    if (nx < 1 || ny < 1 || nz < 1 || nsm < 0) return fail(MPDATA_EINVAL, "bad dims or nsm");
+    Grid g;
+    g.nx = nx; g.ny = ny; g.nz = nz;
+    for (int d = 0; d < 3; ++d) g.per[d] = periodic[d] != 0;
+    mpdata::BandPlan b{0, 0};
+    const bool use = mpdata::fused_band_plan(g, nsm, &b);
+    *n28 = use ? b.n28 : 0;
+    *n24 = use ? b.n24 : 0;
+    return MPDATA_OK;
+}
+
 int mpdata_get_bands(const mpdata_t *m, int *n28, int *n24) {
     if (!m || !n28 || !n24) return fail(MPDATA_EINVAL, "NULL argument");
     *n28 = m->banded ? m->band.n28 : 0;

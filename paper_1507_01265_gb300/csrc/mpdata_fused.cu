@@ -497,6 +497,8 @@ bool fused_band_plan(const Grid &g, int nsm, BandPlan *plan) {
     const long long ntx = (g.nx + 31) / 32;
     const long long w24 = (ntx * ((g.ny + 23) / 24) + nsm - 1) / nsm, w28 = (ntx * ((g.ny + 27) / 28) + nsm - 1) / nsm;
     const double single = std::min(w24 * t24, w28 * t28);
+    // beyond 48 waves the last one is under 2 % of the step: not worth planning
+    if (std::min(w24, w28) > 48) return false;
     double best = 0.0;
     for (int n28 = 1; 28 * n28 < g.ny; ++n28) {
         const int n24 = (g.ny - 28 * n28 + 23) / 24;
