@@ -119,8 +119,8 @@ int mpdata_destroy(mpdata_t *handle);
  * stage path.  Errors: EINVAL (NULL argument). */
 int mpdata_get_tile(const mpdata_t *handle, int *tile_x, int *tile_y);
 
-/* Row bands of a default-tile handle (FP32, fused, iterations 2, x and y
- * periodic, nx % 4 == 0, when the tile model predicts them faster): each step
+/* Row bands of a default-tile handle (FP32, fused, iterations 2, nx % 4 == 0,
+ * when the tile model predicts them faster): each step
  * runs rows [0, 28 * n28) in 32x28 tiles and the rest in n24 bands of 32x24
  * tiles (the last may end past ny), as two launches that run concurrently
  * (a stream and two events owned by the handle fork from and join back into
@@ -133,8 +133,7 @@ int mpdata_get_bands(const mpdata_t *handle, int *n28, int *n24);
 /* The row-band plan mpdata_create would take for an FP32 nx x ny x nz grid
  * with the default tile on a device of nsm SMs (host only, no device call):
  * *n28, *n24 as in mpdata_get_bands, 0 and 0 for one tile shape.  Plans are
- * considered for x/y-periodic grids with nx % 4 == 0 and at most 48 waves of
- * tiles.  Errors: EINVAL (NULL argument, dims < 1, nsm < 0). */
+ * considered for grids with nx % 4 == 0 and at most 48 waves of tiles.  Errors: EINVAL (NULL argument, dims < 1, nsm < 0). */
 int mpdata_plan_bands(int nx, int ny, int nz, const int *periodic, int nsm, int *n28, int *n24);
 
 /* Advance psi by nsteps MPDATA steps in place (async on `stream`): each

@@ -441,7 +441,7 @@ void fused_default_tile(int dtype, const Grid &g, int nsm, int *tx, int *ty) {
     struct Cand { int tx, ty; double us_aligned, us_any, us_ws; };
     static const Cand cands[] = {
         // two-column kernel (16-byte loads if nx % 4 == 0); warp-specialised
-        // form when also x and y are periodic
+        // form when nx % 4 == 0
         {32, 24, 1.94, 2.27, 1.89},
         {32, 28, 2.28, 2.89, 2.28},  // 18 warps at 96 registers: slow alone, fast in full waves
         {32, 16, 1.56, 1.75, 1.56},
@@ -449,7 +449,7 @@ void fused_default_tile(int dtype, const Grid &g, int nsm, int *tx, int *ty) {
         {16, 16, 1.45, 1.45, 1.45},
     };
     const int sms = nsm > 0 ? nsm : 1 << 30;  // unknown device: every grid is one wave
-    const bool aligned = g.nx % 4 == 0, ws = aligned && g.per[0] && g.per[1];
+    const bool aligned = g.nx % 4 == 0, ws = aligned;  // the 32x24 tile runs warp-specialised
     double best = 0.0;
     for (const Cand &c : cands) {
         const long long tiles = (long long)((g.nx + c.tx - 1) / c.tx) * ((g.ny + c.ty - 1) / c.ty);
@@ -493,7 +493,7 @@ bool fused_band_plan(const Grid &g, int nsm, BandPlan *plan) {
     // join (1024x512: predicted 8.78 us-planes, measured 8.71, i.e. 53.97
     // against 51.57 Gcell-steps/s for 32x28 alone).
     const double t28 = 2.28, t24 = 1.89;
-    if (nsm <= 0 || g.nx % 4 != 0 || !g.per[0] || !g.per[1]) return false;
+    if (nsm <= 0 || g.nx % 4 != 0) return false;
     const long long ntx = (g.nx + 31) / 32;
     const long long w24 = (ntx * ((g.ny + 23) / 24) + nsm - 1) / nsm, w28 = (ntx * ((g.ny + 27) / 28) + nsm - 1) / nsm;
     const double single = std::min(w24 * t24, w28 * t28);

@@ -95,7 +95,7 @@ cudaError_t launch_fused_pairs_batch(int tile_x, int tile_y, int nonosc, int lid
 cudaError_t launch_fused_pairs(const Grid &g, int nonosc, double eps, int tile_x, int tile_y,
                                const void *h, const void *psi, const void *u1, const void *u2,
                                const void *u3, void *out, cudaStream_t s);
-// Row bands of an FP32 grid (x and y periodic, nx % 4 == 0): rows [0, 28 n28)
+// Row bands of an FP32 grid with nx % 4 == 0: rows [0, 28 n28)
 // in 32x28 tiles and [28 n28, ny) in 32x24 tiles (the last band may end past
 // ny), launched concurrently on s and s2 (fork and join through the events)
 // so that the hardware mixes the two tile sizes over the SMs.

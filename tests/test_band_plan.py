@@ -46,7 +46,7 @@ def test_known_plans(mp):
     assert mp.plan_bands(2048, 1024, 64) == (4, 38)
     assert mp.plan_bands(4096, 2048, 32) == (0, 0)      # 0.8 % predicted: below the 1 % bar
     assert mp.plan_bands(512, 512, 64) == (0, 0)        # two waves of 32x28 tiles already fit
-    assert mp.plan_bands(1024, 512, 64, (0, 1, 0)) == (0, 0)   # a lid on x: no banded form
+    assert mp.plan_bands(1024, 512, 64, (0, 1, 0)) == (14, 5)  # lids on x or y band the same way
     assert mp.plan_bands(1026, 512, 64) == (0, 0)       # nx % 4 != 0
     assert mp.plan_bands(1024, 512, 64, nsm=0) == (0, 0)
     assert mp.plan_bands(1024, 65535, 8) == (0, 0)      # beyond 48 waves

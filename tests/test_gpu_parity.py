@@ -364,8 +364,9 @@ def test_default_tile_choice():
 
 
 @pytest.mark.parametrize("nonosc", [True, False])
-@pytest.mark.parametrize("nx,ny,nz,bands", [(1024, 512, 4, (14, 5)), (2048, 1024, 2, (4, 38))])
-def test_row_bands(nx, ny, nz, bands, nonosc):
+@pytest.mark.parametrize("nx,ny,nz,bands,per", [(1024, 512, 4, (14, 5), (1, 1, 0)), (2048, 1024, 2, (4, 38), (1, 1, 0)),
+                                                (1024, 512, 3, (14, 5), (1, 0, 1)), (1024, 512, 3, (14, 5), (0, 1, 0))])
+def test_row_bands(nx, ny, nz, bands, per, nonosc):
     """With the default tile a large x/y-periodic grid runs in rows of 32x28
     and 32x24 bands, two concurrent launches per step.  Every cell is computed
     by the same arithmetic as with one tile shape: the banded result equals
@@ -374,12 +375,12 @@ def test_row_bands(nx, ny, nz, bands, nonosc):
     import paper_1507_01265_gb300 as mp
     if torch.cuda.get_device_properties(0).multi_processor_count != 152:
         pytest.skip("band plans are tuned for 152 SMs")
-    f = rand_problem((nz, ny, nx), seed=ny + nz, periodic=(1, 1, 0))
-    with mp.Solver(nx, ny, nz, periodic=(1, 1, 0)) as s:
+    f = rand_problem((nz, ny, nx), seed=ny + nz, periodic=per)
+    with mp.Solver(nx, ny, nz, periodic=per) as s:
         assert s.bands == bands
     banded = run_gpu(f, 3, nonosc=nonosc)
     for tile in ((32, 28), (32, 24)):
-        with mp.Solver(nx, ny, nz, periodic=(1, 1, 0), tile=tile) as s:
+        with mp.Solver(nx, ny, nz, periodic=per, tile=tile) as s:
             assert s.bands == (0, 0)
         assert np.array_equal(banded, run_gpu(f, 3, tile=tile, nonosc=nonosc)), tile
 
@@ -416,9 +417,11 @@ def test_row_bands_in_a_cuda_graph():
 @pytest.mark.parametrize("nonosc", [True, False])
 @pytest.mark.parametrize("nx,ny,nz,per", [
     (96, 50, 9, (1, 1, 0)), (128, 61, 7, (1, 1, 1)), (64, 24, 33, (1, 1, 0)), (32, 5, 4, (1, 1, 1)),
+    (96, 50, 9, (0, 1, 0)), (128, 61, 7, (1, 0, 1)), (64, 57, 12, (0, 0, 0)), (40, 30, 10, (0, 1, 1)),
+    (4, 3, 2, (0, 0, 0)), (8, 52, 5, (1, 0, 0)),
 ])
 def test_warp_specialised_tile(nx, ny, nz, per, nonosc):
-    """32x24 tiles of x/y-periodic grids with nx % 4 == 0 run the
+    """32x24 tiles of grids with nx % 4 == 0 (lids on x or y included) run the
     warp-specialised kernel (producer warps: loads and donor pass).  It
     matches the oracle and, bit for bit, the batched kernel, which runs the
     same tile without specialisation."""
