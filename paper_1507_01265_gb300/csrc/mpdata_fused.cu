@@ -438,22 +438,21 @@ void fused_default_tile(int dtype, const Grid &g, int nsm, int *tx, int *ty) {
     // one CTA, waves = ceil(tiles / SMs) (one CTA per SM).  Per-plane times
     // measured on GB300 (us, nz 33..63): a small grid (one wave) wants the
     // smallest, fastest plane; a large one the most cells per plane-time.
-    struct Cand { int tx, ty; double us_aligned, us_any, us_ws; };
+    struct Cand { int tx, ty; double us_aligned, us_any; };
     static const Cand cands[] = {
-        // two-column kernel (16-byte loads if nx % 4 == 0); warp-specialised
-        // form when nx % 4 == 0
-        {32, 24, 1.94, 2.27, 1.89},
-        {32, 28, 2.28, 2.89, 2.28},  // 18 warps at 96 registers: slow alone, fast in full waves
-        {32, 16, 1.56, 1.75, 1.56},
-        {24, 16, 1.76, 1.76, 1.76},  // one-column kernel
-        {16, 16, 1.45, 1.45, 1.45},
+        // two-column kernel; with nx % 4 == 0 (16-byte loads) the 32x24 tile
+        // runs warp-specialised (1.94 unspecialised)
+        {32, 24, 1.89, 2.27},
+        {32, 28, 2.28, 2.89},  // 18 warps at 96 registers: slow alone, fast in full waves
+        {32, 16, 1.56, 1.75},
+        {24, 16, 1.76, 1.76},  // one-column kernel
+        {16, 16, 1.45, 1.45},
     };
     const int sms = nsm > 0 ? nsm : 1 << 30;  // unknown device: every grid is one wave
-    const bool aligned = g.nx % 4 == 0, ws = aligned;  // the 32x24 tile runs warp-specialised
     double best = 0.0;
     for (const Cand &c : cands) {
         const long long tiles = (long long)((g.nx + c.tx - 1) / c.tx) * ((g.ny + c.ty - 1) / c.ty);
-        const double t = (double)((tiles + sms - 1) / sms) * (ws ? c.us_ws : aligned ? c.us_aligned : c.us_any);
+        const double t = (double)((tiles + sms - 1) / sms) * (g.nx % 4 == 0 ? c.us_aligned : c.us_any);
         if (best == 0.0 || t < best * 0.98) { best = t; *tx = c.tx; *ty = c.ty; }
     }
 }
