@@ -716,7 +716,7 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": dict(workload_config(), path=args.path, tile=list(solver.tile), bands=list(bands),
-                           l2="inputs 671 MB + output 134 MB per launch > 129 MB L2 (no flush)",
+                           l2="inputs 671 MB + output 134 MB per step > 129 MB L2 (no flush)",
                            parallelism="replicas" if world > 1 else "single"),
             "roofline": roofline, "e2e": e2e, "cpu_baseline": cpu,
             "clocks": clk.summary(), "gpu_launches": launches,
