@@ -31,6 +31,8 @@
 // The 32x24 tile of a grid with nx % 4 == 0 runs a warp-specialised form
 // (k_fused_ws): producer warps load and run the donor pass, consumer warps
 // the rest.
+#include <type_traits>
+
 #include "mpdata_internal.cuh"
 
 namespace mpdata {
@@ -98,7 +100,7 @@ __device__ __forceinline__ F2 pseudo_velocity(F2 U, F2 pR, F2 pL, F2 psum, F2 sp
     return sub(mul(sub(fabs2(U), mul(U, t)), A), mul(t8, fma2(ua, Ba, mul(ub, Bb))));
 }
 
-template <int TX, int TY>
+template <int TX, int TY, int NR_ = 5>
 struct Lay2 {
     static_assert(TX % 4 == 0, "TX must be a multiple of 4");
     static constexpr int HX = TX / 2;           // output pairs per row
@@ -114,7 +116,7 @@ struct Lay2 {
     static constexpr int CPR = EX / 4;          // 16-byte chunks per plane row
     static constexpr int NCH = CPR * EY;
     static_assert(NCH <= NT, "one load chunk per thread");
-    static constexpr int NR = 5;                // input ring depth: planes p-2 .. p+2
+    static constexpr int NR = NR_;              // input ring depth (planes)
     static constexpr int RING = 0, P1 = 5 * NR, SX = P1 + 2, SY = SX + 2, SZ = SY + 2;
     static constexpr int V1 = SZ + 1, V2 = V1 + 1, BU = V2 + 1, BD = BU + 1, GX = BD + 1, GY = GX + 1;
     static constexpr int NPLANES = GY + 1;
@@ -184,13 +186,26 @@ __device__ __forceinline__ void stp(unsigned b, F2 v) {
     asm volatile("st.shared.v2.f32 [%0+%1], {%2,%3};" ::"r"(b), "n"(OFF), "f"(v.x), "f"(v.y) : "memory");
 }
 
+// ---------------------------------------------------------------------------
 // One tile (tile index `tile` of grid a.g, tiles numbered row-major with
 // a.ntx tiles per row) marched through all z planes by the whole CTA.
 // AL: 1 = nx % 4 == 0 (16-byte loads, 8-byte stores), 0 = any nx (4-byte
 // loads, per-column stores), 2 = decided per tile from nx.
+// Inputs sit in a 4-plane ring: plane p in slot (p - p_first) & 3, its loads
+// issued after the second barrier of iteration p - 2, into the slot that
+// plane p - 4 has just freed (it arrives within one iteration).  The interior
+// iterations (3 <= p <= nz - 3: every stage active, every load inside the
+// grid) run in blocks of four whose slot offsets are compile-time constants
+// and which carry no z-range checks; the first and last few iterations run
+// one body that checks the z range and computes the slots at run time.
+template <int V>
+using IC = std::integral_constant<int, V>;
+using BT = std::integral_constant<bool, true>;
+using BF = std::integral_constant<bool, false>;
+
 template <int TX, int TY, bool NONOSC, bool LID, int AL>
 __device__ __forceinline__ void pairs_tile(const TileArgs &a, int tile, float *sm) {
-    using L = Lay2<TX, TY>;
+    using L = Lay2<TX, TY, 4>;
     const Grid &g = a.g;
     const float eps1 = a.eps;
     const float *__restrict__ h = a.h;
@@ -204,7 +219,6 @@ __device__ __forceinline__ void pairs_tile(const TileArgs &a, int tile, float *s
     constexpr int PB = PL * 4;         // bytes per plane
     constexpr int FB = L::NR * PB;     // bytes between ring fields
     constexpr int RB = EX * 4;         // bytes per plane row
-    // plane offsets (bytes) of the non-ring planes
     constexpr int oP1 = L::P1 * PB, oSX = L::SX * PB, oSY = L::SY * PB, oSZ = L::SZ * PB;
     constexpr int oV1 = L::V1 * PB, oV2 = L::V2 * PB, oBU = L::BU * PB, oBD = L::BD * PB;
     constexpr int oGX = L::GX * PB, oGY = L::GY * PB;
@@ -219,14 +233,12 @@ __device__ __forceinline__ void pairs_tile(const TileArgs &a, int tile, float *s
 
     int px, ry;
     onion2<TX, TY>(t, px, ry);
-    const int gx = x0 + 2 * px - 4, gy = y0 + ry;  // global column of .x, row
+    const int gx = x0 + 2 * px - 4, gy = y0 + ry;
     const unsigned tb = sm_base + (unsigned)((ry + 3) * EX + 2 * px) * 4u;
-    // lid handling (LID only): clamped neighbours, zero-velocity lid faces
     const bool clampL = LID && !perx && gx == 0;
     const bool clampR = LID && !perx && gx + 1 == nx - 1;
-    const int dD = (LID && !pery && gy == 0) ? 0 : -RB;       // clamped row below (bytes)
-    const int dU = (LID && !pery && gy == ny - 1) ? 0 : RB;   // clamped row above
-    // with odd nx the last column is the .x of a pair: its right ghost clamps to itself
+    const int dD = (LID && !pery && gy == 0) ? 0 : -RB;
+    const int dU = (LID && !pery && gy == ny - 1) ? 0 : RB;
     const bool clampRx = LID && AL != 1 && !perx && gx == nx - 1;
     const bool a16 = AL == 1 || (AL == 2 && (nx & 3) == 0);
     const bool xlid0 = LID && !perx && (gx <= 0 || gx >= nx);
@@ -237,31 +249,27 @@ __device__ __forceinline__ void pairs_tile(const TileArgs &a, int tile, float *s
     const bool store = in_out && gx < nx && gy < ny;
     float *const outp = out + (long long)gy * nx + gx;
 
-    // cell-field pairs one row down/up (clamped on a y-lid)
     auto ldD = [&](unsigned b) { if constexpr (LID) return ldp<0>(b + dD); else return ldp<-RB>(b); };
     auto ldU = [&](unsigned b) { if constexpr (LID) return ldp<0>(b + dU); else return ldp<RB>(b); };
-    // pairs shifted by one column, (col-1, col) and (col+1, col+2): cell
-    // fields clamp on an x-lid, face fields do not
-    auto lshC = [&](unsigned b, F2 own) { float a = lds<-4>(b); return make_float2(clampL ? own.x : a, own.x); };
+    auto lshC = [&](unsigned b, F2 own) { float v = lds<-4>(b); return make_float2(clampL ? own.x : v, own.x); };
     auto rshC = [&](unsigned b, F2 own) {
-        float a = lds<8>(b);
-        return make_float2(clampRx ? own.x : own.y, clampR ? own.y : a);
+        float v = lds<8>(b);
+        return make_float2(clampRx ? own.x : own.y, clampR ? own.y : v);
     };
     auto lshF = [&](unsigned b, F2 own) { return make_float2(lds<-4>(b), own.x); };
     auto rshF = [&](unsigned b, F2 own) { return make_float2(own.y, lds<8>(b)); };
-    auto lid2 = [&](F2 v, bool a, bool c) { return make_float2(a ? 0.f : v.x, c ? 0.f : v.y); };
-
+    auto lid2 = [&](F2 v, bool c0, bool c1) { return make_float2(c0 ? 0.f : v.x, c1 ? 0.f : v.y); };
     // ---- this thread's share of the radius-3 plane loads ----
     // nx % 4 == 0: one 16-byte chunk (4 columns of one row) per thread and
     // field.  Any other nx: 4-byte copies of plane elements t, t + NT, ...,
     // so that a warp reads 128 contiguous bytes and writes consecutive words.
-    constexpr int NE = (PL + L::NT - 1) / L::NT;  // 4-byte elements per thread and field
+    constexpr int NE = (PL + L::NT - 1) / L::NT;
     const bool has_chunk = t < L::NCH;
     int ld_off = 0;
     bool z_all = false, z_u2 = false, patch_u1 = false;
     unsigned ld_dst = 0;
     int e_off[NE];
-    unsigned e_flags = 0;  // per element: bit 3r zero (lid ghost), 3r+1 y-lid face, 3r+2 x-lid face
+    unsigned e_flags = 0;
     if (a16) {
         if (has_chunk) {
             const int ey = t / L::CPR, cc = t % L::CPR;
@@ -270,9 +278,9 @@ __device__ __forceinline__ void pairs_tile(const TileArgs &a, int tile, float *s
             bool outx = false, outy = false;
             if (perx) cx = wrap(lx, nx); else { outx = lx < 0 || lx >= nx; cx = outx ? 0 : lx; }
             if (pery) cy = wrap(ly, ny); else { outy = ly < 0 || ly >= ny; cy = outy ? 0 : ly; }
-            z_all = outx || outy;                    // lid ghost: never read as a cell value
-            z_u2 = z_all || (!pery && ly == 0);      // y-lid face 0
-            patch_u1 = LID && !perx && lx == 0;      // x-lid face 0 is this chunk's first element
+            z_all = outx || outy;
+            z_u2 = z_all || (!pery && ly == 0);
+            patch_u1 = LID && !perx && lx == 0;
             ld_off = cy * nx + cx;
             ld_dst = sm_base + (unsigned)(ey * EX + 4 * cc) * 4u;
         }
@@ -294,12 +302,16 @@ __device__ __forceinline__ void pairs_tile(const TileArgs &a, int tile, float *s
             }
         }
     }
-    auto issue = [&](int p) {
+    // loads of plane p into ring byte offset so; an interior plane (E false)
+    // needs no wrap, clamp or z-lid face
+    auto issue = [&](auto Ec, int p, unsigned so) {
+        constexpr bool E = decltype(Ec)::value;
         if (a16) {
             if (has_chunk) {
-                const long long pc = (long long)(perz ? wrap(p, nz) : min(max(p, 0), nz - 1)) * nxy + ld_off;
-                const bool zz = !perz && (p <= 0 || p >= nz);  // z-lid face
-                const unsigned d = ld_dst + (unsigned)(slot5(p) * PB);
+                const long long pz = E ? (long long)(perz ? wrap(p, nz) : min(max(p, 0), nz - 1)) : (long long)p;
+                const long long pc = pz * nxy + ld_off;
+                const bool zz = E && !perz && (p <= 0 || p >= nz);
+                const unsigned d = ld_dst + so;
                 cp16(d, psi + pc, z_all);
                 cp16(d + FB, u1 + pc, z_all);
                 cp16(d + 2 * FB, u2 + pc, z_u2);
@@ -307,9 +319,9 @@ __device__ __forceinline__ void pairs_tile(const TileArgs &a, int tile, float *s
                 cp16(d + 4 * FB, h + pc, z_all);
             }
         } else {
-            const long long pz = (long long)(perz ? wrap(p, nz) : min(max(p, 0), nz - 1)) * nxy;
-            const bool zz = !perz && (p <= 0 || p >= nz);  // z-lid face
-            const unsigned d0 = sm_base + (unsigned)(t * 4 + slot5(p) * PB);
+            const long long pz = (E ? (long long)(perz ? wrap(p, nz) : min(max(p, 0), nz - 1)) : (long long)p) * nxy;
+            const bool zz = E && !perz && (p <= 0 || p >= nz);
+            const unsigned d0 = sm_base + (unsigned)(t * 4) + so;
 #pragma unroll
             for (int r = 0; r < NE; ++r) {
                 if (t + r * L::NT < PL) {
@@ -334,60 +346,47 @@ __device__ __forceinline__ void pairs_tile(const TileArgs &a, int tile, float *s
     const int wlo = perz ? -2 : 0, whi = perz ? nz : nz - 2;
     const int vlo = perz ? -1 : 0, vhi = perz ? nz : nz - 1;
 
-    // Schedule of iteration p (q1 = p-1, q2 = p-2, q3 = p-3), three barriers:
-    //   alpha: x/y divergence of q3 from neighbour fluxes | pair sums at q1 |
-    //          x/y pseudo-velocities at q2                               -> F
-    //   beta:  z-face pseudo-velocity above q2, extrema and limiter factors
-    //          at q2; wait for the loads of plane p+1                    -> H
-    //   gamma: limited corrective fluxes at q2, output of q3, donor pass
-    //          of plane p (one plane ahead, filling the warps that the
-    //          flux stage leaves idle)                                   -> X
-    // Inputs load two planes ahead into a 5-plane ring, so planes p-2 .. p+1
-    // stay readable for the whole iteration while p+2 streams in.
     const F2 Z = bc(0.f);
-    F2 pn_mm = Z, pn_m = Z, pn_c = Z;     // psi^n at q2-1, q2, q1
-    F2 p1a = Z, p1b = Z, p1c = Z;         // psi1 at q2-1, q2, q1
-    F2 u1b = Z, u2b = Z, u3b = Z, hb = bc(1.f);   // own inputs at q2
-    F2 u1c = Z, u2c = Z, u3c = Z, hc = bc(1.f);   // own inputs at q1
+    F2 pn_mm = Z, pn_m = Z, pn_c = Z;
+    F2 p1a = Z, p1b = Z, p1c = Z;
+    F2 u1b = Z, u2b = Z, u3b = Z, hb = bc(1.f);
+    F2 u1c = Z, u2c = Z, u3c = Z, hc = bc(1.f);
     F2 sxa = Z, sxb = Z, sya = Z, syb = Z;
     F2 wlo_v = Z, bu_prev = Z, bd_prev = Z, h_prev = bc(1.f);
     F2 dacc = Z, gx_own = Z, gy_own = Z;
 
-    issue(p_first);
-    issue(p_first + 1);
-#pragma unroll 2
-    for (int p = p_first; p <= p_last; ++p) {
+    // Iteration p: alpha | beta | gamma as in pairs_tile.  K = (p - p_first) & 3
+    // (or -1: from p at run time); E: check the z range of every stage.
+    auto body = [&](auto Kc, auto Ec, const int p) {
+        constexpr int K = decltype(Kc)::value;
+        constexpr bool E = decltype(Ec)::value;
         const int q1 = p - 1, q2 = p - 2, q3 = p - 3;
-        if (p + 2 <= p_last) issue(p + 2);
-        else asm volatile("cp.async.commit_group;\n" ::: "memory");
-
-        // slot bases of this iteration
-        const unsigned r2 = tb + (unsigned)(slot5(q2) * PB);    // ring, plane q2
-        const unsigned r1 = tb + (unsigned)(slot5(q1) * PB);    // ring, plane q1
-        const unsigned rp = tb + (unsigned)(slot5(p) * PB);     // ring, plane p
-        const unsigned rp1 = tb + (unsigned)(slot5(p + 1) * PB);  // ring, plane p+1
-        const unsigned b1 = tb + (unsigned)((q1 & 1) * PB);     // psi1/SX/SY slot of q1
-        const unsigned b2 = tb + (unsigned)((q2 & 1) * PB);     // psi1/SX/SY slot of q2 (= p)
-
+        const int kk = K >= 0 ? K : ((p - p_first) & 3);
+        const unsigned r2 = tb + (unsigned)(((kk + 2) & 3) * PB);   // ring, plane q2
+        const unsigned r1 = tb + (unsigned)(((kk + 3) & 3) * PB);   // ring, plane q1
+        const unsigned rp = tb + (unsigned)(kk * PB);               // ring, plane p
+        const unsigned rp1 = tb + (unsigned)(((kk + 1) & 3) * PB);  // ring, plane p+1
+        const unsigned b1 = tb + (unsigned)(((kk + 1) & 1) * PB);   // psi1/SX/SY slot of q1
+        const unsigned b2 = tb + (unsigned)((kk & 1) * PB);         // ... of q2 (= of p)
 
         // ---- alpha ----
-        if (in_out && q3 >= 0 && q3 <= nz - 1) {
+        if (in_out && (!E || (q3 >= 0 && q3 <= nz - 1))) {
             const F2 gxr = rshF(tb + oGX, gx_own), gyu = ldp<oGY + RB>(tb);
             dacc = add(add(sub(gxr, gx_own), sub(gyu, gy_own)), dacc);
         }
         F2 sxc = sxb, syc = syb, v1_own = Z, v2_own = Z, pl = Z, pd = Z;
-        if (q1 >= q1lo && q1 <= q1top) {
+        if (!E || (q1 >= q1lo && q1 <= q1top)) {
             sxc = add(lshC(b1 + oP1, p1c), p1c);
             syc = add(ldp<oP1 - RB>(b1), p1c);
             stp<oSX>(b1, sxc);
             stp<oSY>(b1, syc);
             stp<oSZ>(tb, add(p1b, p1c));
         }
-        if (!perz && q1 == 0) { p1b = p1c; sxb = sxc; syb = syc; }
-        if (in_v && q2 >= vlo && q2 <= vhi) {
+        if (E && !perz && q1 == 0) { p1b = p1c; sxb = sxc; syb = syc; }
+        if (in_v && (!E || (q2 >= vlo && q2 <= vhi))) {
             pl = lshF(b2 + oP1, p1b);
             pd = ldp<oP1 - RB>(b2);
-            {   // x-faces: B_y from the x-pair sums above/below, B_z from the own queue
+            {
                 const F2 u2U = ldp<2 * FB + RB>(r2);
                 const F2 ua = add(add(add(lshF(r2 + 2 * FB, u2b), u2b),
                                       make_float2(lds<2 * FB + RB - 4>(r2), u2U.x)), u2U);
@@ -396,7 +395,7 @@ __device__ __forceinline__ void pairs_tile(const TileArgs &a, int tile, float *s
                                              ub, add(lshF(r2 + 4 * FB, hb), hb), eps);
                 v1_own = LID ? lid2(v, xlid0, xlid1) : v;
             }
-            {   // y-faces: B_z from the own queue, B_x from the y-pair sums left/right
+            {
                 const F2 u1D = ldp<FB - RB>(r2);
                 const F2 va = add(add(add(ldp<3 * FB - RB>(r2), u3b), ldp<3 * FB - RB>(r1)), u3c);
                 const F2 vb = add(add(add(u1D, u1b), make_float2(u1D.y, lds<FB - RB + 8>(r2))),
@@ -413,14 +412,14 @@ __device__ __forceinline__ void pairs_tile(const TileArgs &a, int tile, float *s
         // ---- beta ----
         F2 whi_v = Z, bu_c = Z, bd_c = Z;
         if (in_beta) {
-            if (q2 >= wlo && q2 <= whi) {
+            if (!E || (q2 >= wlo && q2 <= whi)) {
                 const F2 szo = add(p1b, p1c);
                 const F2 ua = add(add(add(u1b, u1c), rshF(r2 + FB, u1b)), rshF(r1 + FB, u1c));
                 const F2 ub = add(add(add(u2b, u2c), ldp<2 * FB + RB>(r2)), ldp<2 * FB + RB>(r1));
                 whi_v = pseudo_velocity(u3c, p1c, p1b, szo, rshC(tb + oSZ, szo), lshC(tb + oSZ, szo), ua,
                                         ldU(tb + oSZ), ldD(tb + oSZ), ub, add(hb, hc), eps);
             }
-            if (NONOSC && q2 >= vlo && q2 <= vhi) {
+            if (NONOSC && (!E || (q2 >= vlo && q2 <= vhi))) {
                 const F2 aL = lshC(r2, pn_m), aR = rshC(r2, pn_m), aD = ldD(r2), aU = ldU(r2);
                 const F2 bL = lshC(b2 + oP1, p1b), bR = rshC(b2 + oP1, p1b);
                 const F2 bD = ldD(b2 + oP1), bU = ldU(b2 + oP1);
@@ -440,12 +439,15 @@ __device__ __forceinline__ void pairs_tile(const TileArgs &a, int tile, float *s
                 stp<oBD>(tb, bd_c);
             }
         }
-        asm volatile("cp.async.wait_group 1;\n" ::: "memory");  // plane p+1 landed
-        if (LID && patch_u1) sm[(ld_dst - sm_base) / 4u + (unsigned)(L::RING * PL + L::NR * PL + slot5(p + 1) * PL)] = 0.f;
+        asm volatile("cp.async.wait_group 0;\n" ::: "memory");  // plane p+1 landed
+        if (LID && patch_u1)
+            sm[(ld_dst - sm_base) / 4u + (unsigned)(L::NR * PL + ((kk + 1) & 3) * PL)] = 0.f;
         __syncthreads();  // (H)
+        // plane p+2 into the slot of q2, which no stage reads any more
+        if (!E || p + 2 <= p_last) issue(Ec, p + 2, (unsigned)(((kk + 2) & 3) * PB));
 
         // ---- gamma ----
-        if (in_vm && q2 >= 0 && q2 <= nz - 1) {
+        if (in_vm && (!E || (q2 >= 0 && q2 <= nz - 1))) {
             F2 vm1 = v1_own, vm2 = v2_own;
             if (NONOSC) {
                 const F2 buL = lshF(tb + oBU, bu_c), bdL = lshF(tb + oBD, bd_c);
@@ -463,10 +465,10 @@ __device__ __forceinline__ void pairs_tile(const TileArgs &a, int tile, float *s
             stp<oGX>(tb, gx_own);
             stp<oGY>(tb, gy_own);
         }
-        const bool q3ok = q3 >= 0 && q3 <= nz - 1, q2ok = q2 >= 0 && q2 <= nz - 1;
+        const bool q3ok = !E || (q3 >= 0 && q3 <= nz - 1), q2ok = !E || (q2 >= 0 && q2 <= nz - 1);
         if (in_out && (q3ok || q2ok)) {
             F2 gz = Z;
-            if (perz || (q2 >= 1 && q2 <= nz - 1)) {
+            if (!E || perz || (q2 >= 1 && q2 <= nz - 1)) {
                 F2 vm3 = wlo_v;
                 if (NONOSC) {
                     const F2 one = bc(1.f);
@@ -479,18 +481,18 @@ __device__ __forceinline__ void pairs_tile(const TileArgs &a, int tile, float *s
                 float *const o = outp + (long long)q3 * nxy;
                 if (a16) {
                     st2(o, v);
-                } else {  // any nx: the pair may end past nx and need not be 8-byte aligned
+                } else {
                     o[0] = v.x;
                     if (gx + 1 < nx) o[1] = v.y;
                 }
             }
             dacc = sub(Z, gz);
         }
-        // (a1) donor pass at plane p (psi^n at p-1, p, p+1)
-        F2 p1n = p1c;  // lid top ghost: zero-gradient copy of the plane below
+        // (a1) donor pass at plane p
+        F2 p1n = p1c;
         const F2 pn_p = ldp<0>(rp);
         const F2 u1p = ldp<FB>(rp), u2p = ldp<2 * FB>(rp), u3p = ldp<3 * FB>(rp), hp = ldp<4 * FB>(rp);
-        if (p >= q1lo && p <= q1hi) {
+        if (!E || (p >= q1lo && p <= q1hi)) {
             const F2 pn_n = ldp<0>(rp1);
             const F2 u3n = ldp<3 * FB>(rp1);
             const F2 fxl = flux(u1p, lshC(rp, pn_p), pn_p);
@@ -502,7 +504,7 @@ __device__ __forceinline__ void pairs_tile(const TileArgs &a, int tile, float *s
             const F2 div = add(add(sub(fxh, fxl), sub(fyh, fyl)), sub(fzh, fzl));
             p1n = sub(pn_p, mul(div, rcp(hp)));
         }
-        if (p >= q1lo && p <= q1top) stp<oP1>(b2, p1n);  // slot of p == slot of q2 (no longer read)
+        if (!E || (p >= q1lo && p <= q1top)) stp<oP1>(b2, p1n);
         __syncthreads();  // (X)
 
         h_prev = hb;
@@ -512,9 +514,33 @@ __device__ __forceinline__ void pairs_tile(const TileArgs &a, int tile, float *s
         p1a = p1b; p1b = p1c; p1c = p1n;
         sxa = sxb; sxb = sxc; sya = syb; syb = syc;
         wlo_v = whi_v; bu_prev = bu_c; bd_prev = bd_c;
+    };
+
+    issue(BT(), p_first, 0u);
+    issue(BT(), p_first + 1, (unsigned)PB);
+    const int n_iter = p_last - p_first + 1;
+    // interior iterations 3 <= p <= nz - 3, in whole blocks of four starting
+    // at an iteration index that is a multiple of four
+    const int i_s = (3 - p_first + 3) & ~3;
+    const int nblk = max(0, nz - 3 - p_first + 1 - i_s) >> 2;
+#pragma unroll 1
+    for (int i = 0; i < n_iter;) {
+        if (i == i_s && nblk > 0) {
+#pragma unroll 1
+            for (int b = 0; b < nblk; ++b, i += 4) {
+                const int p = p_first + i;
+                body(IC<0>(), BF(), p);
+                body(IC<1>(), BF(), p + 1);
+                body(IC<2>(), BF(), p + 2);
+                body(IC<3>(), BF(), p + 3);
+            }
+            continue;
+        }
+        body(IC<-1>(), BT(), p_first + i);
+        ++i;
     }
     asm volatile("cp.async.wait_all;\n" ::: "memory");
-    __syncthreads();  // shared memory is reused by the next tile of a persistent CTA
+    __syncthreads();
 }
 
 // ---------------------------------------------------------------------------
@@ -925,7 +951,7 @@ __global__ void __launch_bounds__(Lay2<TX, TY>::NT, 1)
 template <int TX, int TY>
 cudaError_t launch_pairs(const Grid &g, int nonosc, double eps, const void *h, const void *psi,
                          const void *u1, const void *u2, const void *u3, void *out, cudaStream_t s) {
-    using L = Lay2<TX, TY>;
+    using L = Lay2<TX, TY, 4>;  // the two-column kernel's 4-plane ring
     const size_t smem = (size_t)L::NPLANES * L::PL * sizeof(float);
     const int ntx = (g.nx + TX - 1) / TX, nty = (g.ny + TY - 1) / TY;
     const bool lid = !g.per[0] || !g.per[1];
@@ -964,7 +990,7 @@ cudaError_t launch_pairs(const Grid &g, int nonosc, double eps, const void *h, c
 template <int TX, int TY>
 cudaError_t launch_pairs_batch(int nonosc, int lid, const BatchGrid *grids, const int2 *items,
                                const int *begin, int ncta, int parity, cudaStream_t s) {
-    using L = Lay2<TX, TY>;
+    using L = Lay2<TX, TY, 4>;  // the two-column kernel's 4-plane ring
     const size_t smem = (size_t)L::NPLANES * L::PL * sizeof(float);
     auto kern = nonosc ? (lid ? k_fused_pairs_batch<TX, TY, true, true> : k_fused_pairs_batch<TX, TY, true, false>)
                        : (lid ? k_fused_pairs_batch<TX, TY, false, true> : k_fused_pairs_batch<TX, TY, false, false>);
@@ -996,7 +1022,7 @@ cudaError_t launch_fused_bands(const Grid &g, int nonosc, double eps, const Band
                                const void *psi, const void *u1, const void *u2, const void *u3,
                                void *out, cudaStream_t s, cudaStream_t s2, cudaEvent_t ev_fork,
                                cudaEvent_t ev_join) {
-    using L28 = Lay2<32, 28>;
+    using L28 = Lay2<32, 28, 4>;
     using L24 = Lay2<32, 24>;
     if (g.nx % 4 != 0 || plan.n28 < 1 || plan.n24 < 1) return cudaErrorInvalidValue;
     const bool lid = !g.per[0] || !g.per[1];
