@@ -26,7 +26,10 @@ Workloads (the paper's own runs are synthetic MPDATA domains of
     periodic x/y and rigid lids in z (the 1024x512x64 roofline case and the
     2048x1024x64 precision case);
   * ``tracer_batch``: independent grids with log-uniform sizes and
-    per-grid constant Courant vectors (the batched-launch case).
+    per-grid constant Courant vectors (the batched-launch case);
+  * ``near_zero_blobs`` / ``truncated_blobs``: narrower blobs on a 1e-6
+    background, or on exact zeros with a jump at a cutoff (the psi -> 0
+    regime of the limiter).
 """
 from __future__ import annotations
 
@@ -229,6 +232,32 @@ def precision_grid(nx=2048, ny=1024, nz=64, nsteps=100, seed=1512) -> Fields:
     background, so that values span six decades."""
     f = rotation_blobs(nx=nx, ny=ny, nz=nz, background=1e-6, nsteps=nsteps, seed=seed)
     return dataclasses.replace(f, name="precision_%dx%dx%d" % (nx, ny, nz))
+
+
+def near_zero_blobs(nx, ny, nz, background=1e-6, nblobs=4, sigma=(2.0, 6.0), max_c=0.5,
+                    nsteps=10, seed=1513, periodic=(1, 1, 0)) -> Fields:
+    """The psi -> 0 regime of the limiter: rotation field, sine density and
+    seeded Gaussian blobs (sigma U[2, 6], amplitude U[1, 4]) on a 1e-6
+    background, so that values span six decades and the limiter's
+    denominators are dominated by eps over most of the grid."""
+    st = Stream(seed)
+    shape = (nz, ny, nx)
+    blobs = draw_blobs(st, nblobs, nx, ny, nz, sigma=sigma)
+    psi = gaussian_sum(shape, tuple(bool(p) for p in periodic), background, blobs)
+    u1, u2, u3 = rotation_courant(nx, ny, nz, max_c)
+    return Fields("near_zero_%dx%dx%d" % (nx, ny, nz), nx, ny, nz, tuple(periodic),
+                  sine_density(nx, ny, nz), _f32(psi), u1, u2, u3, nsteps, seed)
+
+
+def truncated_blobs(nx, ny, nz, cutoff=1e-3, nblobs=4, sigma=(2.0, 6.0), max_c=0.5,
+                    nsteps=10, seed=1514, periodic=(1, 1, 0)) -> Fields:
+    """Exact zeros: the blobs of near_zero_blobs on background 0 with every
+    value below `cutoff` set to exactly 0, so that most of the grid is zero
+    and every blob ends in a jump of about `cutoff`."""
+    f = near_zero_blobs(nx, ny, nz, background=0.0, nblobs=nblobs, sigma=sigma, max_c=max_c,
+                        nsteps=nsteps, seed=seed, periodic=periodic)
+    psi = np.where(f.psi.astype(np.float64) < cutoff, 0.0, f.psi.astype(np.float64))
+    return dataclasses.replace(f, name="truncated_%dx%dx%d" % (nx, ny, nz), psi=_f32(psi))
 
 
 def subsample(f: Fields, every=8, max_c=0.5) -> Fields:

@@ -31,7 +31,11 @@
  * Errors: every entry point returns MPDATA_OK (0) or a negative MPDATA_E*
  * code; nothing aborts, traps or prints.  mpdata_strerror() names a code and
  * mpdata_last_error_message() gives the detail of the calling thread's last
- * failure.  A handle is used by one host thread at a time.
+ * failure.  A handle is used by one host thread at a time.  A handle's
+ * device scratch is shared by its calls: mpdata_step uses its psi-sized
+ * ping-pong buffer, mpdata_mass and mpdata_courant_max its reduction
+ * partials, so the calls on one handle must run in order on one stream (or
+ * be serialised by the caller); calls on different streams race on them.
  */
 #ifndef MPDATA_H
 #define MPDATA_H
@@ -229,7 +233,11 @@ int mpdata_courant_max(mpdata_t *handle, const void *h, const void *u1, const vo
  * allocating call is made.  Limit: n must be in [1, 2^31 - 1] (EINVAL
  * otherwise).  The first call on each device looks up the array's device
  * address (cudaGetSymbolAddress) with that device current; make that first
- * call before any stream capture.  All calls share the one array and every
+ * call before any stream capture.  The address is cached per device ordinal
+ * and belongs to that device's primary context (the one the CUDA runtime
+ * uses): it does not survive cudaDeviceReset, and a caller that makes a
+ * different driver context current on the same device must not use this
+ * entry point from it.  All calls share the one array and every
  * call overwrites all partials it reads, so nothing has to start at zero --
  * but calls whose kernels overlap on the GPU (other streams, other threads)
  * race on it and must be serialised by the caller.

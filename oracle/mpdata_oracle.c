@@ -20,11 +20,16 @@
  *
  * With iterations = 3 stages (a2)-(a6) run a second time on the result of
  * the first corrective pass, the pseudo-velocities now built from the
- * limited velocities that pass used in place of the Courant numbers (each
- * corrective pass estimates the error of the pass before it, Smolarkiewicz
- * 1984 §3).  Parity unpinned: under the limiter, that the second pass is
- * built from the limited (not the raw) velocities of the first is a
- * reading; no pin separates the two (they coincide without the limiter).
+ * limited velocities that pass used in place of the Courant numbers.  Each
+ * corrective pass estimates the truncation error of the pass before it
+ * (Smolarkiewicz 1984, §3, the iterated scheme), and under the
+ * nonoscillatory option every iteration's pseudo-velocity is limited before
+ * it transports anything (Smolarkiewicz & Grabowski 1990, §3): the pass
+ * before the second corrective one is therefore the limited transport, and
+ * its velocities are the limited ones.  Parity unpinned: that the second
+ * pass is built from the limited (not the raw) velocities of the first is
+ * this reading of Smolarkiewicz & Grabowski (1990), §3; no pin separates the
+ * two (they coincide without the limiter).
  *
  * The formulas follow the published MPDATA scheme: the basic two-pass scheme
  * with its cross terms (Smolarkiewicz 1984, J. Comput. Phys. 54), the
@@ -346,7 +351,9 @@ static int run_step(const oracle_cfg *c, const double *h, const double *psi,
 
     if (c->iterations == 3) {
         /* second corrective pass: psi2 corrected, pseudo-velocities built
-         * from the velocities the first corrective pass transported with */
+         * from the velocities the first corrective pass transported with
+         * (the limited ones under the nonoscillatory option: Smolarkiewicz &
+         * Grabowski 1990, §3, limit every iteration before it transports) */
         for (int d = 0; d < 3; ++d) memcpy(wprev[d], vm[d], sizeof(double) * n);
         const double *w2[3] = {wprev[0], wprev[1], wprev[2]};
         corrective_pass(c, h, psi, psi2, w2, v, vm, bup, bdn, out);

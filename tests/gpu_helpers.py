@@ -42,10 +42,21 @@ def run_gpu(f: F.Fields, nsteps, dtype="f32", path="fused", iterations=2, nonosc
     return t[1].double().cpu().numpy()
 
 
-def run_oracle(f: F.Fields, nsteps, iterations=2, nonosc=True, extrema="both"):
+def oracle_lib(omp=True):
+    """The oracle's OpenMP build (same bits as the serial one, all host
+    cores) when it loads, else the serial build."""
+    if omp:
+        try:
+            return oracle.load(omp=True)
+        except Exception:  # noqa: BLE001  (no OpenMP on this host)
+            pass
+    return oracle.load()
+
+
+def run_oracle(f: F.Fields, nsteps, iterations=2, nonosc=True, extrema="both", omp=False):
     cfg = oracle.Config(f.nx, f.ny, f.nz, tuple(f.periodic), iterations, int(nonosc), 1e-15,
                         {"both": 0, "corrected": 1}[extrema])
-    return oracle.run(cfg, *f.as_f64(), nsteps=nsteps)
+    return oracle.run(cfg, *f.as_f64(), nsteps=nsteps, lib=oracle_lib() if omp else None)
 
 
 def rel_err(got, want):

@@ -1,12 +1,13 @@
 """Batched launches: every grid of a batch gives exactly (bit for bit) what
 mpdata_step gives on that grid alone, whatever the mix of grids, the work
 split between CTAs (one CTA per tile by default, balanced persistent, uneven),
-odd or even step counts, or graph replay."""
+odd or even step counts, or graph replay -- and matches the FP64 oracle
+(max |dpsi| <= 1e-5 max|psi| for up to 10 steps)."""
 import numpy as np
 import pytest
 
 import gen.fields as F
-from gpu_helpers import rand_problem, run_gpu
+from gpu_helpers import rand_problem, rel_err, run_gpu, run_oracle
 
 pytestmark = pytest.mark.gpu
 
@@ -50,8 +51,10 @@ def test_batch_equals_alone(mp, nsteps, graph, nonosc):
         b.step(nsteps, graph=graph)  # a second run reuses the cached graph
         torch.cuda.synchronize()
     for f, t in zip(fs, ts):
+        got = t[1].double().cpu().numpy()
         alone = run_gpu(f, 2 * nsteps, nonosc=nonosc, tile=(32, 24))  # the batch tile
-        assert np.array_equal(t[1].double().cpu().numpy(), alone), f.name
+        assert np.array_equal(got, alone), f.name
+        assert rel_err(got, run_oracle(f, 2 * nsteps, nonosc=nonosc, omp=True)) <= 1e-5, f.name
 
 
 def test_uneven_and_degenerate_splits(mp):
@@ -73,7 +76,9 @@ def test_uneven_and_degenerate_splits(mp):
         b.step(3)
         torch.cuda.synchronize()
     for f, t in zip(fs, ts):
-        assert np.array_equal(t[1].double().cpu().numpy(), run_gpu(f, 3, tile=(32, 16))), f.name
+        got = t[1].double().cpu().numpy()
+        assert np.array_equal(got, run_gpu(f, 3, tile=(32, 16))), f.name
+        assert rel_err(got, run_oracle(f, 3, omp=True)) <= 1e-5, f.name
 
 
 @pytest.mark.parametrize("graph", [False, True])
@@ -110,6 +115,7 @@ def test_default_and_balanced_splits(mp, graph):
     for f, a, c in zip(fs, *results):
         alone = run_gpu(f, 3, tile=(32, 24))
         assert np.array_equal(a, alone) and np.array_equal(c, alone), f.name
+        assert rel_err(a, run_oracle(f, 3, omp=True)) <= 1e-5, f.name
 
 
 def test_bad_split_is_rejected(mp):
@@ -144,7 +150,9 @@ def test_per_grid_tiles(mp, graph):
         b.step(3, graph=graph)
         torch.cuda.synchronize()
     for f, t, ty in zip(fs, ts, tiles):
-        assert np.array_equal(t[1].double().cpu().numpy(), run_gpu(f, 3, tile=(32, ty or 24))), (f.name, ty)
+        got = t[1].double().cpu().numpy()
+        assert np.array_equal(got, run_gpu(f, 3, tile=(32, ty or 24))), (f.name, ty)
+        assert rel_err(got, run_oracle(f, 3, omp=True)) <= 1e-5, (f.name, ty)
 
 
 def test_bad_tile_heights_are_rejected(mp):

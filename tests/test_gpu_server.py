@@ -1,6 +1,7 @@
 """Serving: requests of mixed sizes and step counts admitted by HBM budget,
 batched as they arrive; each result equals the request run alone (bit for
-bit).  Failure handling is exercised on the host: over-budget submits,
+bit) and matches the FP64 oracle (max |dpsi| <= 1e-5 max|psi| up to 10
+steps, <= 1e-4 beyond).  Failure handling is exercised on the host: over-budget submits,
 timeouts, cancellation and an injected allocation failure."""
 import threading
 
@@ -8,7 +9,7 @@ import numpy as np
 import pytest
 
 import gen.fields as F
-from gpu_helpers import run_gpu
+from gpu_helpers import rel_err, run_gpu, run_oracle
 
 pytestmark = pytest.mark.gpu
 
@@ -60,7 +61,10 @@ def test_results_equal_alone_in_the_mix(mp):
         st = srv.stats()
         assert st["completed"] == len(fs) and st["resident"] == 0 and st["admitted_bytes"] == 0
     for f, o in zip(fs, outs):
-        assert np.array_equal(o.astype(np.float64), run_gpu(f, f.nsteps, tile=(32, 24))), f.name
+        got = o.astype(np.float64)
+        assert np.array_equal(got, run_gpu(f, f.nsteps, tile=(32, 24))), f.name
+        tol = 1e-5 if f.nsteps <= 10 else 1e-4
+        assert rel_err(got, run_oracle(f, f.nsteps)) <= tol, f.name
 
 
 def test_budget_refusal_timeout_cancel(mp):
