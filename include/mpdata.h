@@ -303,18 +303,35 @@ int mpdata_batch_destroy(mpdata_batch_t *batch);
  * (No counterpart in the paper: a front end that runs many independent
  * solves of the §5.2 step on one GPU.)
  *
- * A server owns a scheduler thread and a CUDA stream on the device current at
- * creation.  Requests (host fields, FP32) are admitted first-in first-out
- * while their device footprint (6 fields: h, psi, psi scratch, u1, u2, u3)
- * fits the HBM budget and fewer than max_active are resident; every tick
- * advances all resident requests by the same chunk of steps in one persistent
- * batched launch per kernel variant (see mpdata_batch_*), so requests that
- * arrive while others run join at the next tick and share the GPU.  A
- * finished request's psi is copied back into its host buffer, then its
- * memory and budget are released.  Each result is bit-identical to
- * mpdata_step on that grid alone with tile 32 x tile_y.  Host buffers must stay valid until the
- * request finishes; pinned memory keeps the scheduler from blocking on
- * copies.  All entry points are thread-safe. */
+ * A server owns a scheduler thread and three CUDA streams on the device
+ * current at creation: one for the ticks, one for copies in, one for copies
+ * out.  Requests (host fields, FP32) are admitted first-in first-out while
+ * their device footprint (6 fields: h, psi, psi scratch, u1, u2, u3) fits
+ * the HBM budget and fewer than max_active are resident.  An admitted
+ * request's fields are copied in on the copy-in stream while the ticks of the
+ * requests already resident go on; it joins the ticks once its copy has
+ * landed.  Every tick advances all resident requests by the same chunk of
+ * steps in one batched launch per kernel variant (see mpdata_batch_*), so
+ * requests that arrive while others run join a later tick and share the GPU.
+ * A finished request's psi is copied back into its host buffer on the
+ * copy-out stream (after the tick that finished it, without holding up the
+ * next one), then its memory and budget are released.  Each result is
+ * bit-identical to mpdata_step on that grid alone with tile 32 x tile_y.
+ * Host buffers must stay valid until the request finishes; pinned memory
+ * keeps the scheduler from blocking on copies.
+ *
+ * Tickets: a finished request (DONE, FAILED or CANCELLED) stays known to
+ * mpdata_poll, mpdata_wait and mpdata_request_times until mpdata_release is
+ * called on it, or until more than retain_finished requests that finished
+ * later are still held, whichever comes first; after that its ticket gives
+ * ENOENT.  A request that a thread is waiting on is not retired until that
+ * wait returns.  So a server that runs indefinitely holds at most
+ * retain_finished finished requests (plus those queued or resident).
+ *
+ * All entry points are thread-safe.  mpdata_server_destroy may be called
+ * while other threads are blocked in mpdata_wait: they return (ECANCELED for
+ * requests it cancelled) before it frees anything.  No thread may start a
+ * call on the server once mpdata_server_destroy has been called. */
 #define MPDATA_REQ_QUEUED 0    /* waiting for budget or a slot */
 #define MPDATA_REQ_RUNNING 1   /* resident on the device */
 #define MPDATA_REQ_DONE 2      /* psi holds the result */
@@ -333,6 +350,9 @@ typedef struct mpdata_server_opts {
     int32_t nonoscillatory;     /* default 1 */
     int32_t inject_alloc_failure; /* test hook: every n-th admission fails as out of memory (0 = off) */
     double eps;                 /* default 1e-15 */
+    int32_t retain_finished;    /* finished requests kept queryable before the oldest are
+                                   retired (default 65536; 0 = retire each one as soon as it
+                                   has finished and nobody waits on it) */
 } mpdata_server_opts;
 
 typedef struct mpdata_request {
@@ -362,10 +382,18 @@ int mpdata_wait(mpdata_server_t *server, uint64_t ticket, int timeout_ms);
 int mpdata_cancel(mpdata_server_t *server, uint64_t ticket);
 /* Submit, admit and finish times of a request, seconds since server start. */
 int mpdata_request_times(mpdata_server_t *server, uint64_t ticket, double *t3);
+/* Forget a finished request: its ticket gives ENOENT from now on.  Errors:
+ * ENOENT (unknown or already retired), EBUSY (not finished yet, or a thread
+ * is waiting on it). */
+int mpdata_release(mpdata_server_t *server, uint64_t ticket);
+/* *count = requests the server holds: queued, resident, being copied out,
+ * and finished ones not yet released or retired. */
+int mpdata_server_retained(mpdata_server_t *server, uint64_t *count);
 /* stats[0..5]: completed, cell-steps done, admitted bytes, queued, resident,
  * seconds since start. */
 int mpdata_server_stats(mpdata_server_t *server, double *stats);
-/* Cancel queued work, stop the scheduler, free everything. */
+/* Cancel queued and resident work, stop the scheduler, release the threads
+ * blocked in mpdata_wait, free everything. */
 int mpdata_server_destroy(mpdata_server_t *server);
 
 /* ---- functional-performance-model partitioning (§2-§4) ----

@@ -314,13 +314,15 @@ class Server:
 
     def __init__(self, hbm_budget_bytes: int = 8 << 30, *, max_active: int = 256,
                  max_queued: int = 1 << 20, chunk_steps: int = 8, tile_y: int = 24,
-                 nonoscillatory: bool = True, inject_alloc_failure: int = 0, eps: float = 1e-15):
+                 nonoscillatory: bool = True, inject_alloc_failure: int = 0, eps: float = 1e-15,
+                 retain_finished: int = 1 << 16):
         o = _lib.ServerOpts()
         _lib.lib.mpdata_server_opts_default(ctypes.byref(o))
         o.hbm_budget_bytes = int(hbm_budget_bytes)
         o.max_active, o.max_queued, o.chunk_steps = int(max_active), int(max_queued), int(chunk_steps)
         o.tile_y, o.nonoscillatory = int(tile_y), int(bool(nonoscillatory))
         o.inject_alloc_failure, o.eps = int(inject_alloc_failure), float(eps)
+        o.retain_finished = int(retain_finished)
         self._h = ctypes.c_void_p()
         check(_lib.lib.mpdata_server_create(ctypes.byref(o), ctypes.byref(self._h)),
               "mpdata_server_create")
@@ -362,7 +364,7 @@ class Server:
 
     def wait(self, ticket: int, timeout_ms: int = -1) -> None:
         rc = _lib.lib.mpdata_wait(self._h, ctypes.c_uint64(ticket), int(timeout_ms))
-        if rc == _lib.MPDATA_OK:
+        if rc != _lib.MPDATA_ETIMEDOUT:  # finished (or unknown): the server is done with the buffers
             self._keep.pop(ticket, None)
         check(rc, "mpdata_wait")
 
@@ -374,6 +376,17 @@ class Server:
         t = (ctypes.c_double * 3)()
         check(_lib.lib.mpdata_request_times(self._h, ctypes.c_uint64(ticket), t), "mpdata_request_times")
         return tuple(t)
+
+    def release(self, ticket: int) -> None:
+        """Forget a finished request (mpdata_release)."""
+        check(_lib.lib.mpdata_release(self._h, ctypes.c_uint64(ticket)), "mpdata_release")
+        self._keep.pop(ticket, None)
+
+    def retained(self) -> int:
+        """Requests the server still holds (mpdata_server_retained)."""
+        n = ctypes.c_uint64()
+        check(_lib.lib.mpdata_server_retained(self._h, ctypes.byref(n)), "mpdata_server_retained")
+        return n.value
 
     def stats(self) -> dict:
         v = (ctypes.c_double * 6)()

@@ -45,7 +45,7 @@ class ServerOpts(ctypes.Structure):
                 ("max_active", ctypes.c_int32), ("max_queued", ctypes.c_int32),
                 ("chunk_steps", ctypes.c_int32), ("tile_y", ctypes.c_int32),
                 ("nonoscillatory", ctypes.c_int32), ("inject_alloc_failure", ctypes.c_int32),
-                ("eps", ctypes.c_double)]
+                ("eps", ctypes.c_double), ("retain_finished", ctypes.c_int32)]
 
 
 class Request(ctypes.Structure):
@@ -102,6 +102,8 @@ def _load():
         "mpdata_wait": (I, [H, ctypes.c_uint64, I]),
         "mpdata_cancel": (I, [H, ctypes.c_uint64]),
         "mpdata_request_times": (I, [H, ctypes.c_uint64, ctypes.POINTER(ctypes.c_double)]),
+        "mpdata_release": (I, [H, ctypes.c_uint64]),
+        "mpdata_server_retained": (I, [H, ctypes.POINTER(ctypes.c_uint64)]),
         "mpdata_server_stats": (I, [H, ctypes.POINTER(ctypes.c_double)]),
         "mpdata_server_destroy": (I, [H]),
         "mpdata_fpm_algorithm1": (I, [D, I, D, P, P, I, ctypes.POINTER(D), ctypes.POINTER(D), ctypes.POINTER(D)]),

@@ -1,21 +1,30 @@
 // Serving runtime (C ABI in include/mpdata.h: mpdata_server_*, mpdata_submit,
-// mpdata_poll, mpdata_wait, mpdata_cancel, mpdata_request_times).
+// mpdata_poll, mpdata_wait, mpdata_cancel, mpdata_release,
+// mpdata_request_times).
 //
-// A scheduler thread owns one CUDA stream and runs continuous batching:
+// A scheduler thread runs continuous batching on three CUDA streams:
 //   * admission: queued requests (FIFO) are admitted while their device
 //     footprint (h, psi, scratch, u1, u2, u3) fits the HBM budget and a slot is
-//     free; their fields are copied in on the stream;
+//     free; their memory is allocated and their fields copied in on the
+//     copy-in stream, and an event marks the end of the copy;
+//   * a loading request joins the resident set once that event has
+//     completed, so its copy runs on a copy engine under the ticks of the
+//     requests already resident instead of in front of them;
 //   * tick: every resident request is advanced by the same chunk of steps
-//     (chunk = min(chunk_steps, fewest remaining)); each step is one batched
-//     launch per kernel variant over the tiles of all resident requests, one
-//     CTA per tile, largest tiles first (the same kernels and tiles as a
-//     single-grid step, so each result is bit-identical to running that
-//     request alone);
-//   * completion: a finished request's psi is copied back to its host buffer,
-//     its device memory is freed and its budget released once the copy is
-//     done; requests that arrive meanwhile join at the next tick.
-// Host-side waits are bounded (mpdata_wait takes a timeout); nothing on the
-// device waits on anything.
+//     (chunk = min(chunk_steps, fewest remaining)) on the tick stream; each
+//     step is one batched launch per kernel variant over the tiles of all
+//     resident requests, one CTA per tile, largest tiles first (the same
+//     kernels and tiles as a single-grid step, so each result is
+//     bit-identical to running that request alone);
+//   * completion: the copy-out stream waits for the tick that finished a
+//     request, copies its psi back to the host buffer and frees its device
+//     memory; the budget is released once that copy is done.  Requests that
+//     arrive meanwhile join at a later tick.
+// Finished requests stay queryable until mpdata_release, or until more than
+// retain_finished newer requests have finished (the oldest go first); a
+// request that a thread is waiting on is never retired.  Host-side waits are
+// bounded (mpdata_wait takes a timeout); nothing on the device waits on
+// anything.
 #include <stdarg.h>
 #include <stdio.h>
 #include <string.h>
@@ -63,9 +72,22 @@ struct Request {
     int variant = kPairsPeriodic, ntiles = 0;
     BatchGrid bg;  // buf[0] holds the current state, buf[1] its partner
     float *dev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
-    cudaEvent_t done_ev = nullptr;
+    cudaEvent_t ready_ev = nullptr;  // copy-in done (copy-in stream)
+    cudaEvent_t done_ev = nullptr;   // copy-out done (copy-out stream)
+    int waiters = 0;                 // threads inside mpdata_wait on this request
     double t_submit = 0, t_admit = 0, t_done = 0;
 };
+
+bool terminal(const Request *r) {
+    return r->state == MPDATA_REQ_DONE || r->state == MPDATA_REQ_FAILED ||
+           r->state == MPDATA_REQ_CANCELLED;
+}
+
+void destroy_events(Request *r) {
+    if (r->ready_ev) cudaEventDestroy(r->ready_ev);
+    if (r->done_ev) cudaEventDestroy(r->done_ev);
+    r->ready_ev = r->done_ev = nullptr;
+}
 
 struct TickBuffers {
     BatchGrid *d_grids = nullptr;
@@ -88,12 +110,15 @@ double now_s(Clock::time_point t0) {
 struct mpdata_server {
     mpdata_server_opts o;
     int device = 0;
-    cudaStream_t stream = nullptr;
+    cudaStream_t stream = nullptr;                            // ticks
+    cudaStream_t copy_in = nullptr, copy_out = nullptr;       // admissions, results
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
     std::deque<Request *> queue;
-    std::vector<Request *> active, copying;
+    std::vector<Request *> loading, active, copying;
     std::unordered_map<uint64_t, Request *> all;
+    std::deque<uint64_t> finished_order;  // tickets in the order they finished
+    int waiters = 0;                      // threads inside mpdata_wait
     size_t admitted_bytes = 0, reserved_bytes = 0;
     uint64_t next_ticket = 1;
     unsigned admissions = 0;
@@ -108,11 +133,39 @@ struct mpdata_server {
 
 namespace {
 
-void free_request_device(mpdata_server *s, Request *r) {
+void free_request_device(Request *r, cudaStream_t st) {
     for (auto &p : r->dev) {
-        if (p) cudaFreeAsync(p, s->stream);
+        if (p) cudaFreeAsync(p, st);
         p = nullptr;
     }
+}
+
+// Retire finished requests beyond the retained count, oldest first, skipping
+// any that a thread is waiting on (lock held).
+void retire_excess(mpdata_server *s) {
+    const size_t keep = (size_t)s->o.retain_finished;
+    for (auto it = s->finished_order.begin(); s->finished_order.size() > keep && it != s->finished_order.end();) {
+        auto f = s->all.find(*it);
+        if (f == s->all.end()) {  // released already
+            it = s->finished_order.erase(it);
+            continue;
+        }
+        Request *r = f->second;
+        if (r->waiters > 0) {
+            ++it;
+            continue;
+        }
+        destroy_events(r);
+        delete r;
+        s->all.erase(f);
+        it = s->finished_order.erase(it);
+    }
+}
+
+// A request reached DONE, FAILED or CANCELLED (lock held).
+void mark_terminal(mpdata_server *s, Request *r) {
+    s->finished_order.push_back(r->ticket);
+    retire_excess(s);
 }
 
 // Make room for n elements of a device array (synchronises first: the old
@@ -130,19 +183,25 @@ cudaError_t ensure(T **ptr, size_t *cap, size_t n, cudaStream_t st) {
     return e;
 }
 
-void fail_request(mpdata_server *s, Request *r, int code) {
+// An admitted request failed: free its memory on stream st, release its
+// budget, make it terminal (lock held; r may be retired on return).
+void fail_request(mpdata_server *s, Request *r, int code, cudaStream_t st) {
     r->state = MPDATA_REQ_FAILED;
     r->error = code;
     r->t_done = now_s(s->t0);
-    free_request_device(s, r);
+    free_request_device(r, st);
+    destroy_events(r);
+    s->admitted_bytes -= r->bytes;
+    mark_terminal(s, r);
 }
 
-// Allocate and copy in an admitted request (no lock held: only the
-// scheduler thread touches a request between admission and completion).
+// Allocate and start the copy-in of an admitted request on the copy-in
+// stream; ready_ev marks its end (no lock held: only the scheduler thread
+// touches a request between admission and completion).
 int load_request(mpdata_server *s, Request *r, bool injected) {
     cudaError_t e = injected ? cudaErrorMemoryAllocation : cudaSuccess;
     for (int f = 0; f < 6 && e == cudaSuccess; ++f)
-        e = cudaMallocAsync((void **)&r->dev[f], r->field_bytes, s->stream);
+        e = cudaMallocAsync((void **)&r->dev[f], r->field_bytes, s->copy_in);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return MPDATA_ENOMEM;
@@ -150,8 +209,12 @@ int load_request(mpdata_server *s, Request *r, bool injected) {
     const void *src[5] = {r->req.h, r->req.psi, r->req.u1, r->req.u2, r->req.u3};
     float *dst[5] = {r->dev[0], r->dev[1], r->dev[3], r->dev[4], r->dev[5]};
     for (int f = 0; f < 5 && e == cudaSuccess; ++f)
-        e = cudaMemcpyAsync(dst[f], src[f], r->field_bytes, cudaMemcpyHostToDevice, s->stream);
-    if (e != cudaSuccess) return MPDATA_ECUDA;
+        e = cudaMemcpyAsync(dst[f], src[f], r->field_bytes, cudaMemcpyHostToDevice, s->copy_in);
+    if (e == cudaSuccess) e = cudaEventRecord(r->ready_ev, s->copy_in);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return MPDATA_ECUDA;
+    }
     BatchGrid &g = r->bg;
     g.h = r->dev[0];
     g.buf[0] = r->dev[1];
@@ -228,6 +291,7 @@ cudaError_t run_tick(mpdata_server *s, const std::vector<Request *> &act, int ch
     T.in_flight = true;
     s->tick_index++;
     finished.assign(na, 0);
+    bool joined = false;  // copy-out stream ordered after this tick
     for (int a = 0; a < na && e == cudaSuccess; ++a) {
         Request *r = act[a];
         r->remaining -= chunk;
@@ -235,10 +299,14 @@ cudaError_t run_tick(mpdata_server *s, const std::vector<Request *> &act, int ch
         const bool cancel = r->cancel.load();
         if (r->remaining > 0 && !cancel) continue;
         finished[a] = cancel ? 2 : 1;
-        if (!cancel)
-            e = cudaMemcpyAsync(r->req.psi, r->bg.buf[0], r->field_bytes, cudaMemcpyDeviceToHost, s->stream);
-        free_request_device(s, r);
-        if (e == cudaSuccess) e = cudaEventRecord(r->done_ev, s->stream);
+        if (!joined) {
+            e = cudaStreamWaitEvent(s->copy_out, T.ev, 0);
+            joined = true;
+        }
+        if (e == cudaSuccess && !cancel)
+            e = cudaMemcpyAsync(r->req.psi, r->bg.buf[0], r->field_bytes, cudaMemcpyDeviceToHost, s->copy_out);
+        free_request_device(r, s->copy_out);
+        if (e == cudaSuccess) e = cudaEventRecord(r->done_ev, s->copy_out);
     }
     return e;
 }
@@ -255,15 +323,45 @@ void finish_copies(mpdata_server *s) {  // lock held
                 r->state = MPDATA_REQ_DONE;
                 ++s->completed;
             } else {
+                cudaGetLastError();
                 r->state = MPDATA_REQ_FAILED;
                 r->error = MPDATA_ECUDA;
             }
         }
         r->t_done = now_s(s->t0);
+        destroy_events(r);
+        mark_terminal(s, r);
         any = true;
     }
     s->copying.swap(still);
     if (any) s->cv_done.notify_all();
+}
+
+// Loading requests whose copy-in has completed join the resident set (lock
+// held).  Returns true if any request is still loading.
+bool promote_loaded(mpdata_server *s) {
+    std::vector<Request *> still;
+    for (Request *r : s->loading) {
+        cudaError_t q = cudaEventQuery(r->ready_ev);
+        if (q == cudaErrorNotReady) { still.push_back(r); continue; }
+        if (q != cudaSuccess) {
+            cudaGetLastError();
+            fail_request(s, r, MPDATA_ECUDA, s->copy_in);
+            s->cv_done.notify_all();
+        } else if (r->cancel.load() || s->stop) {
+            r->state = MPDATA_REQ_CANCELLED;
+            r->t_done = now_s(s->t0);
+            free_request_device(r, s->copy_in);
+            destroy_events(r);
+            s->admitted_bytes -= r->bytes;
+            mark_terminal(s, r);
+            s->cv_done.notify_all();
+        } else {
+            s->active.push_back(r);
+        }
+    }
+    s->loading.swap(still);
+    return !s->loading.empty();
 }
 
 void scheduler(mpdata_server *s) {
@@ -283,27 +381,34 @@ void scheduler(mpdata_server *s) {
                     r->t_done = now_s(s->t0);
                     if (r->bytes <= s->reserved_bytes) s->reserved_bytes -= r->bytes;
                     it = s->queue.erase(it);
+                    destroy_events(r);
+                    mark_terminal(s, r);
                     s->cv_done.notify_all();
                 } else {
                     ++it;
                 }
             }
+            promote_loaded(s);
             // admission: FIFO while the budget and the slots allow
             while (!s->stop && !s->queue.empty()) {
                 Request *r = s->queue.front();
-                if (s->active.size() + admit.size() >= (size_t)s->o.max_active) break;
+                if (s->active.size() + s->loading.size() + admit.size() >= (size_t)s->o.max_active) break;
                 if (s->admitted_bytes + r->bytes > s->o.hbm_budget_bytes) break;
                 s->queue.pop_front();
                 s->admitted_bytes += r->bytes;
                 if (r->bytes <= s->reserved_bytes) s->reserved_bytes -= r->bytes;
                 ++s->admissions;
+                r->state = MPDATA_REQ_RUNNING;
+                r->t_admit = now_s(s->t0);
                 admit.push_back(r);
                 admit_injected.push_back(s->o.inject_alloc_failure > 0 &&
                                          s->admissions % (unsigned)s->o.inject_alloc_failure == 0);
             }
+            if (s->stop)
+                for (Request *r : s->active) r->cancel.store(true);
             if (s->active.empty() && admit.empty()) {
-                if (s->stop && s->copying.empty()) break;
-                if (!s->copying.empty()) {
+                if (s->stop && s->copying.empty() && s->loading.empty()) break;
+                if (!s->copying.empty() || !s->loading.empty()) {
                     lk.unlock();
                     std::this_thread::sleep_for(std::chrono::microseconds(50));
                 } else {
@@ -311,10 +416,9 @@ void scheduler(mpdata_server *s) {
                 }
                 continue;
             }
-            if (s->stop)
-                for (Request *r : s->active) r->cancel.store(true);
         }
-        // copy-in of the admitted requests (no lock)
+        // copy-in of the admitted requests (no lock): enqueued on the copy-in
+        // stream; they join the ticks once their copies have landed
         std::vector<int> load_rc(admit.size());
         for (size_t i = 0; i < admit.size(); ++i) load_rc[i] = load_request(s, admit[i], admit_injected[i]);
         {
@@ -322,14 +426,11 @@ void scheduler(mpdata_server *s) {
             for (size_t i = 0; i < admit.size(); ++i) {
                 Request *r = admit[i];
                 if (load_rc[i] != MPDATA_OK) {
-                    fail_request(s, r, load_rc[i]);
-                    s->admitted_bytes -= r->bytes;
+                    fail_request(s, r, load_rc[i], s->copy_in);
                     s->cv_done.notify_all();
                     continue;
                 }
-                r->state = MPDATA_REQ_RUNNING;
-                r->t_admit = now_s(s->t0);
-                s->active.push_back(r);
+                s->loading.push_back(r);
             }
             act = s->active;
         }
@@ -343,8 +444,7 @@ void scheduler(mpdata_server *s) {
             for (size_t a = 0; a < act.size(); ++a) {
                 Request *r = act[a];
                 if (e != cudaSuccess) {
-                    fail_request(s, r, MPDATA_ECUDA);
-                    s->admitted_bytes -= r->bytes;
+                    fail_request(s, r, MPDATA_ECUDA, s->stream);
                     continue;
                 }
                 s->cell_steps += (double)r->req.nx * r->req.ny * r->req.nz * chunk;
@@ -363,6 +463,8 @@ void scheduler(mpdata_server *s) {
         }
     }
     cudaStreamSynchronize(s->stream);
+    cudaStreamSynchronize(s->copy_in);
+    cudaStreamSynchronize(s->copy_out);
 }
 
 }  // namespace
@@ -381,6 +483,7 @@ void mpdata_server_opts_default(mpdata_server_opts *o) {
     o->nonoscillatory = 1;
     o->inject_alloc_failure = 0;
     o->eps = 1e-15;
+    o->retain_finished = 1 << 16;
 }
 
 int mpdata_server_create(const mpdata_server_opts *opts, mpdata_server_t **out) {
@@ -393,15 +496,21 @@ int mpdata_server_create(const mpdata_server_opts *opts, mpdata_server_t **out) 
     if (o.max_active < 1 || o.max_queued < 0 || o.chunk_steps < 1) return sfail(MPDATA_EINVAL, "max_active >= 1, max_queued >= 0, chunk_steps >= 1");
     if (o.tile_y != 16 && o.tile_y != 24) return sfail(MPDATA_EINVAL, "tile_y must be 16 or 24");
     if (!(o.eps > 0.0)) return sfail(MPDATA_EINVAL, "eps must be > 0");
+    if (o.retain_finished < 0) return sfail(MPDATA_EINVAL, "retain_finished must be >= 0");
     mpdata_server *s = new (std::nothrow) mpdata_server();
     if (!s) return sfail(MPDATA_ENOMEM, "host allocation failed");
     s->o = o;
     cudaError_t e = cudaGetDevice(&s->device);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->copy_in, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->copy_out, cudaStreamNonBlocking);
     for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&s->tick[i].ev, cudaEventDisableTiming);
     if (e != cudaSuccess) {
         cudaGetLastError();
-        if (s->stream) cudaStreamDestroy(s->stream);
+        for (auto &T : s->tick)
+            if (T.ev) cudaEventDestroy(T.ev);
+        for (cudaStream_t st : {s->stream, s->copy_in, s->copy_out})
+            if (st) cudaStreamDestroy(st);
         delete s;
         return sfail(MPDATA_ECUDA, "server setup: %s", cudaGetErrorString(e));
     }
@@ -446,22 +555,25 @@ int mpdata_submit(mpdata_server_t *s, const mpdata_request *req, uint64_t *ticke
         delete r;
         return sfail(MPDATA_EBUSY, "over the HBM budget and the admission queue is full");
     }
-    if (cudaEventCreateWithFlags(&r->done_ev, cudaEventDisableTiming) != cudaSuccess) {
+    if (req->nsteps > 0 && (cudaEventCreateWithFlags(&r->ready_ev, cudaEventDisableTiming) != cudaSuccess ||
+                            cudaEventCreateWithFlags(&r->done_ev, cudaEventDisableTiming) != cudaSuccess)) {
         cudaGetLastError();
+        destroy_events(r);
         delete r;
         return sfail(MPDATA_ECUDA, "cudaEventCreate failed");
     }
     r->ticket = s->next_ticket++;
     r->t_submit = now_s(s->t0);
-    s->reserved_bytes += r->bytes;
+    s->all[r->ticket] = r;
     if (req->nsteps == 0) {  // nothing to do: psi already holds the answer
         r->state = MPDATA_REQ_DONE;
         r->t_admit = r->t_done = r->t_submit;
-        s->reserved_bytes -= r->bytes;
-    } else {
-        s->queue.push_back(r);
+        *ticket = r->ticket;
+        mark_terminal(s, r);  // (may retire it at once when retain_finished is 0)
+        return MPDATA_OK;
     }
-    s->all[r->ticket] = r;
+    s->reserved_bytes += r->bytes;
+    s->queue.push_back(r);
     *ticket = r->ticket;
     s->cv_work.notify_one();
     return MPDATA_OK;
@@ -482,13 +594,44 @@ int mpdata_wait(mpdata_server_t *s, uint64_t ticket, int timeout_ms) {
     auto it = s->all.find(ticket);
     if (it == s->all.end()) return sfail(MPDATA_ENOENT, "unknown ticket %llu", (unsigned long long)ticket);
     Request *r = it->second;
-    auto finished = [r] { return r->state == MPDATA_REQ_DONE || r->state == MPDATA_REQ_FAILED || r->state == MPDATA_REQ_CANCELLED; };
+    // while counted as a waiter the request is neither retired nor freed by
+    // mpdata_server_destroy
+    ++r->waiters;
+    ++s->waiters;
+    auto finished = [r] { return terminal(r); };
+    bool done = true;
     if (timeout_ms < 0) s->cv_done.wait(lk, finished);
-    else if (!s->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), finished))
+    else done = s->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), finished);
+    const int state = r->state, error = r->error;
+    --r->waiters;
+    if (--s->waiters == 0) s->cv_done.notify_all();  // mpdata_server_destroy may be waiting
+    if (done) retire_excess(s);
+    if (!done)
         return sfail(MPDATA_ETIMEDOUT, "ticket %llu not finished after %d ms", (unsigned long long)ticket, timeout_ms);
-    if (r->state == MPDATA_REQ_DONE) return MPDATA_OK;
-    if (r->state == MPDATA_REQ_CANCELLED) return sfail(MPDATA_ECANCELED, "ticket %llu was cancelled", (unsigned long long)ticket);
-    return sfail(r->error ? r->error : MPDATA_ECUDA, "ticket %llu failed", (unsigned long long)ticket);
+    if (state == MPDATA_REQ_DONE) return MPDATA_OK;
+    if (state == MPDATA_REQ_CANCELLED) return sfail(MPDATA_ECANCELED, "ticket %llu was cancelled", (unsigned long long)ticket);
+    return sfail(error ? error : MPDATA_ECUDA, "ticket %llu failed", (unsigned long long)ticket);
+}
+
+int mpdata_release(mpdata_server_t *s, uint64_t ticket) {
+    if (!s) return sfail(MPDATA_EINVAL, "NULL server");
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->all.find(ticket);
+    if (it == s->all.end()) return sfail(MPDATA_ENOENT, "unknown ticket %llu", (unsigned long long)ticket);
+    Request *r = it->second;
+    if (!terminal(r)) return sfail(MPDATA_EBUSY, "ticket %llu has not finished", (unsigned long long)ticket);
+    if (r->waiters > 0) return sfail(MPDATA_EBUSY, "ticket %llu is being waited on", (unsigned long long)ticket);
+    destroy_events(r);
+    delete r;
+    s->all.erase(it);  // its entry in finished_order is skipped when reached
+    return MPDATA_OK;
+}
+
+int mpdata_server_retained(mpdata_server_t *s, uint64_t *count) {
+    if (!s || !count) return sfail(MPDATA_EINVAL, "NULL argument");
+    std::lock_guard<std::mutex> lk(s->mu);
+    *count = (uint64_t)s->all.size();
+    return MPDATA_OK;
 }
 
 int mpdata_cancel(mpdata_server_t *s, uint64_t ticket) {
@@ -531,14 +674,25 @@ int mpdata_server_destroy(mpdata_server_t *s) {
         s->stop = true;
         for (Request *r : s->queue) {
             r->state = MPDATA_REQ_CANCELLED;
+            r->t_done = now_s(s->t0);
         }
         s->queue.clear();
         s->cv_work.notify_all();
     }
+    // the scheduler cancels resident and loading requests and drains the
+    // copies before it returns: every request is then finished
     if (s->thr.joinable()) s->thr.join();
-    s->cv_done.notify_all();
+    {
+        // release the threads blocked in mpdata_wait and let them read their
+        // request before anything is freed
+        std::unique_lock<std::mutex> lk(s->mu);
+        for (auto &kv : s->all)
+            if (!terminal(kv.second)) kv.second->state = MPDATA_REQ_CANCELLED;
+        s->cv_done.notify_all();
+        s->cv_done.wait(lk, [s] { return s->waiters == 0; });
+    }
     for (auto &kv : s->all) {
-        if (kv.second->done_ev) cudaEventDestroy(kv.second->done_ev);
+        destroy_events(kv.second);
         delete kv.second;
     }
     for (auto &T : s->tick) {
@@ -548,6 +702,8 @@ int mpdata_server_destroy(mpdata_server_t *s) {
         if (T.ev) cudaEventDestroy(T.ev);
     }
     cudaStreamDestroy(s->stream);
+    cudaStreamDestroy(s->copy_in);
+    cudaStreamDestroy(s->copy_out);
     delete s;
     return MPDATA_OK;
 }

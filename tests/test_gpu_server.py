@@ -113,3 +113,75 @@ def test_injected_allocation_failure(mp):
     assert codes == [0, mp._lib.MPDATA_ENOMEM, 0, mp._lib.MPDATA_ENOMEM]
     for i in (0, 2):
         assert np.array_equal(outs[i].astype(np.float64), run_gpu(fs[i], fs[i].nsteps, tile=(32, 24)))
+
+
+def test_finished_requests_are_retired(mp):
+    """A server that runs on holds a bounded number of finished requests: the
+    oldest are retired beyond retain_finished, mpdata_release forgets one at
+    once, and a request still running cannot be released."""
+    f = F.rotation_blobs(nx=16, ny=8, nz=4, nblobs=1, seed=6)
+    keep = 8
+    with mp.Server(hbm_budget_bytes=64 << 20, retain_finished=keep) as srv:
+        tickets = []
+        for i in range(120):
+            tickets.append(srv.submit(f.h, f.psi.copy(), f.u1, f.u2, f.u3, 2, periodic=f.periodic))
+            if i % 10 == 9:
+                for t in tickets[-10:]:
+                    _wait_or_retired(mp, srv, t)
+                assert srv.retained() <= keep
+        assert srv.retained() <= keep
+        with pytest.raises(mp.MpdataError) as e:   # retired long ago
+            srv.poll(tickets[0])
+        assert e.value.code == mp._lib.MPDATA_ENOENT
+        last = tickets[-1]
+        assert srv.poll(last) == mp._lib.REQ_DONE
+        srv.release(last)
+        with pytest.raises(mp.MpdataError) as e:
+            srv.times(last)
+        assert e.value.code == mp._lib.MPDATA_ENOENT
+        busy = srv.submit(f.h, f.psi.copy(), f.u1, f.u2, f.u3, 100000, periodic=f.periodic)
+        with pytest.raises(mp.MpdataError) as e:   # still running
+            srv.release(busy)
+        assert e.value.code == mp._lib.MPDATA_EBUSY
+        srv.cancel(busy)
+        with pytest.raises(mp.MpdataError):
+            srv.wait(busy, timeout_ms=60000)
+        srv.release(busy)
+        assert srv.retained() <= keep
+
+
+def _wait_or_retired(mp, srv, ticket):
+    """Wait for a request; ENOENT means it finished and was retired already."""
+    try:
+        srv.wait(ticket, timeout_ms=60000)
+    except mp.MpdataError as e:
+        assert e.code == mp._lib.MPDATA_ENOENT
+
+
+def test_destroy_releases_blocked_waiters(mp):
+    """Destroying a server while another thread is blocked in mpdata_wait on
+    a running request cancels it and returns that wait (ECANCELED) before
+    anything is freed."""
+    f = F.rotation_blobs(nx=64, ny=64, nz=16, nblobs=1, seed=8)
+    srv = mp.Server(hbm_budget_bytes=64 << 20)
+    t = srv.submit(f.h, f.psi.copy(), f.u1, f.u2, f.u3, 10 ** 7, periodic=f.periodic)
+    codes = []
+    started = threading.Event()
+
+    def waiter():
+        started.set()
+        try:
+            srv.wait(t)
+            codes.append(0)
+        except mp.MpdataError as e:
+            codes.append(e.code)
+
+    th = threading.Thread(target=waiter)
+    th.start()
+    started.wait()
+    import time
+    time.sleep(0.2)  # the waiter is inside mpdata_wait
+    srv.close()
+    th.join(timeout=60)
+    assert not th.is_alive()
+    assert codes == [mp._lib.MPDATA_ECANCELED]
