@@ -70,6 +70,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
+    ap.add_argument("--no-arms", action="store_true",
+                    help="skip the comparison arms (stage path, one tile height, batched splits)")
     ap.add_argument("--workload", default="grid", choices=["grid", "tracers", "serve", "precision"],
                     help="grid: 1024x512x64 (default); tracers: 64 uneven grids batched; "
                          "serve: Poisson arrivals through the serving runtime vs one solve per launch; "
@@ -103,6 +105,14 @@ def max_over_ranks(x, dist, device=None):
     t = torch.tensor([float(x)], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def measured_sm_max_mhz():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["sm_max_mhz"])
+    except Exception:
+        return 2070.0
 
 
 def measured_peaks():
@@ -671,15 +681,23 @@ def main():
                 "peak_kind": peak_kind, "kernel": kname,
                 "algorithmic_bytes_per_step": algo_bytes}
     rec = kernel_record() if args.path == "fused" else None
+    clocks = clk.summary()
+    nsm = torch.cuda.get_device_properties(dev).multi_processor_count
     if rec is not None and "warp_inst_per_cell" in rec:
         # what binds the kernel: instruction issue (one warp instruction per
-        # scheduler per cycle; 4 schedulers per SM)
-        nsm = torch.cuda.get_device_properties(dev).multi_processor_count
-        issue_peak = nsm * 4 * 2070e6 / 1e9
+        # scheduler per cycle; 4 schedulers per SM) at the SM clock sampled
+        # during the timed region
+        mhz, mhz_from = clocks.get("sm_mhz"), "median SM clock sampled in the timed region"
+        if not mhz:
+            mhz, mhz_from = measured_sm_max_mhz(), "maximum SM clock (no samples)"
+        issue_peak = nsm * 4 * mhz * 1e6 / 1e9
         issue_ach = rec["warp_inst_per_cell"] * ncells / launch_s / 1e9
         roofline["issue"] = {"achieved": issue_ach, "peak": issue_peak, "unit": "G warp-inst/s",
-                             "frac": issue_ach / issue_peak,
+                             "frac": issue_ach / issue_peak, "sm_mhz": mhz, "sm_mhz_from": mhz_from,
                              "warp_inst_per_cell": rec["warp_inst_per_cell"]}
+    arms = None
+    if args.path == "fused" and not args.no_arms and tile is None:
+        arms = measure_arms(f, t, stream, nsm)
 
     # end to end through the public host API
     e2e = None
@@ -721,7 +739,7 @@ def main():
                            l2="inputs 671 MB + output 134 MB per step > 129 MB L2 (no flush)",
                            parallelism="replicas" if world > 1 else "single"),
             "roofline": roofline, "e2e": e2e, "cpu_baseline": cpu,
-            "clocks": clk.summary(), "gpu_launches": launches,
+            "clocks": clocks, "gpu_launches": launches, "arms": arms,
             "pct_hbm_roofline": 100.0 * roofline["frac"],
             "ci95_pct": ci95_pct(per_solve),
         }
@@ -730,6 +748,76 @@ def main():
     if dist is not None:
         dist.destroy_process_group()
     return 0
+
+
+def measure_arms(f, t, stream, nsm, reps=3, nsteps=20):
+    """Config 2's comparison arms, each timed in this process on the same
+    grid and fields (CUDA events, best of `reps` runs of `nsteps` steps):
+      fused_default    the production launch (the bench value's kernels)
+      stages           one kernel per stage, every intermediate through HBM
+      tile_32x28       the fused kernel with one tile height, no row bands
+      batch_per_tile   the grid as a one-grid batch (32x24 tiles), one CTA
+                       per tile, handed out by the hardware (default split)
+      batch_balanced   the same with the balanced persistent split: one CTA
+                       per SM, contiguous ranges of equal tile counts
+      batch_fpm        the same with the split the speed-function
+                       partitioner picks (Algorithm 1 generalised, §4) from
+                       speed functions measured with every SM busy (§5.4)
+    The last three go through the batched kernel (per-grid arguments from
+    memory), which is what a split applies to."""
+    import numpy as np
+    import torch
+    import paper_1507_01265_gb300 as mp
+    from paper_1507_01265_gb300 import fpm, tune
+    cells = f.ncells
+    psi0 = t[1].clone()
+
+    def best_ms(run):
+        run()  # warm-up (and graph capture where used)
+        torch.cuda.synchronize()
+        out = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            run()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            out.append(e0.elapsed_time(e1))
+        return min(out)
+
+    def rate(ms):
+        return cells * nsteps / (ms * 1e-3) / 1e9
+
+    arms = {}
+    for name, kw in (("fused_default", {}), ("stages", {"path": "stages"}), ("tile_32x28", {"tile": (32, 28)})):
+        with mp.Solver(f.nx, f.ny, f.nz, periodic=f.periodic, **kw) as s:
+            arms[name] = {"gcell_steps_per_s": rate(best_ms(lambda: s.step(*t, nsteps, stream)))}
+    tile = (32, 24)
+    xs, ss = tune.speed_function(tile, xs=(1, 2, 3, 4, 5, 6), nz=16, steps=4)
+    ntiles = math.ceil(f.nx / tile[0]) * math.ceil(f.ny / tile[1])
+    cond2 = fpm.condition2(xs, ss)[0]
+    k, xl, xr, t_pred = fpm.partition(ntiles, nsm, 1.0, xs, ss / (tile[0] * tile[1] * 16))
+    with mp.Batch([(f.nx, f.ny, f.nz, f.periodic)], tile=tile) as b:
+        b.set_fields(0, *t)
+        v = b.grid_variant(0)
+        run = lambda: b.step(nsteps, graph=True)
+        arms["batch_per_tile"] = {"gcell_steps_per_s": rate(best_ms(run)), "ctas": b.work(v)[1]}
+        b.set_balanced_split(v, nsm)
+        arms["batch_balanced"] = {"gcell_steps_per_s": rate(best_ms(run)), "ctas": b.work(v)[1]}
+        n, ncta = b.work(v)
+        if k > 0:
+            b.set_split(v, tune.split_for(n, ncta, k, xl, xr))
+        arms["batch_fpm"] = {"gcell_steps_per_s": rate(best_ms(run)), "ctas": ncta,
+                             "k_right": k, "x_left": xl, "x_right": xr,
+                             "condition2_holds": bool(cond2),
+                             "speed_function": {"tiles_per_cta": xs.tolist(),
+                                                "cells_per_s_per_cta": [float(v_) for v_ in ss],
+                                                "measured_on": "P*x tiles of 32x24, nz 16, every SM busy"}}
+    t[1].copy_(psi0)
+    for a in arms.values():
+        a["vs_fused_default"] = a["gcell_steps_per_s"] / arms["fused_default"]["gcell_steps_per_s"]
+    arms["_how"] = "best of %d runs of %d steps each, CUDA events, same process and fields" % (reps, nsteps)
+    return arms
 
 
 def ci95_pct(samples):
