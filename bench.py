@@ -519,6 +519,73 @@ def _errors(got, want, background):
             "background_cells": int(bg.sum())}
 
 
+def beta_denominator_study(f, nsteps):
+    """The limiter factors' denominators in the psi -> 0 regime of the
+    precision grid: from the oracle's intermediate fields of step `nsteps`
+    (psi1 and the pseudo-velocities, periodic x/y, lid z), the in/out flux
+    sums IN and OUT evaluated in FP64 and in FP32 (float32 inputs and
+    arithmetic, subnormals flushed as the kernels do), and the limiter
+    factors min(1, beta) that each gives.  A rule that recomputes a
+    denominator in FP64 below a threshold would take that branch for the
+    cells listed in below_threshold."""
+    import numpy as np
+    import oracle
+    cfg = oracle.Config(f.nx, f.ny, f.nz, f.periodic, 2, 1, 1e-15, 0)
+    h, psi0, u1, u2, u3 = f.as_f64()
+    psin = oracle.run(cfg, h, psi0, u1, u2, u3, nsteps=nsteps - 1, lib=oracle_lib()[0])
+    st = oracle.stages(cfg, h, psin, u1, u2, u3)
+    eps = 1e-15
+
+    def ftz(a):
+        a = np.asarray(a, dtype=np.float32)
+        return np.where(np.abs(a) < np.finfo(np.float32).tiny, np.float32(0), a)
+
+    def sums(p1, v, dt):
+        z = lambda a: np.asarray(a, dtype=dt)
+        p1 = z(p1)
+        IN = np.zeros_like(p1)
+        OUT = np.zeros_like(p1)
+        for d, ax in ((0, 2), (1, 1), (2, 0)):  # x, y, z faces; array axes [z][y][x]
+            vlo = z(v[d])
+            vhi = np.roll(vlo, -1, axis=ax)
+            lo_nb = np.roll(p1, 1, axis=ax)
+            hi_nb = np.roll(p1, -1, axis=ax)
+            if not f.periodic[d]:  # lid: no flux through faces 0 and n
+                sl = [slice(None)] * 3
+                sl[ax] = -1
+                vhi[tuple(sl)] = 0
+            pos = lambda a: np.maximum(a, dt(0))
+            neg = lambda a: np.minimum(a, dt(0))
+            IN = IN + (pos(vlo) * lo_nb - neg(vhi) * hi_nb)
+            OUT = OUT + (pos(vhi) * p1 - neg(vlo) * p1)
+            if dt is np.float32:
+                IN, OUT = ftz(IN), ftz(OUT)
+        return IN, OUT
+
+    v = (st["v1"], st["v2"], st["v3"])
+    IN64, OUT64 = sums(st["psi1"], v, np.float64)
+    IN32, OUT32 = sums(ftz(st["psi1"]), tuple(ftz(a) for a in v), np.float32)
+    # numerators (psimax - psi1) h and (psi1 - psimin) h from the oracle's own beta factors
+    num_up = st["beta_up"] * (IN64 + eps)
+    num_dn = st["beta_dn"] * (OUT64 + eps)
+    lim = lambda b: np.minimum(1.0, b)
+    b64u, b64d = lim(num_up / (IN64 + eps)), lim(num_dn / (OUT64 + eps))
+    n32u = np.asarray(num_up, np.float32)
+    n32d = np.asarray(num_dn, np.float32)
+    b32u = lim(n32u / (IN32 + np.float32(eps)).astype(np.float32)).astype(np.float64)
+    b32d = lim(n32d / (OUT32 + np.float32(eps)).astype(np.float32)).astype(np.float64)
+    rel = lambda a, b: float(np.max(np.abs(a - b)))
+    den = np.concatenate([IN64.ravel(), OUT64.ravel()])
+    return {"what": "limiter factors min(1, beta) of step %d on the %dx%dx%d copy: FP32 flux sums vs FP64"
+                    % (nsteps, f.nx, f.ny, f.nz),
+            "max_abs_diff_min1_beta_up": rel(b32u, b64u), "max_abs_diff_min1_beta_dn": rel(b32d, b64d),
+            "max_rel_diff_in_sum": float(np.max(np.abs(IN32 - IN64) / (IN64 + eps))),
+            "max_rel_diff_out_sum": float(np.max(np.abs(OUT32 - OUT64) / (OUT64 + eps))),
+            "below_threshold": {"%g" % tau: float(np.mean(den < tau)) for tau in (1e-30, 1e-20, 1e-15, 1e-12)},
+            "exactly_zero": float(np.mean(den == 0.0)),
+            "min_positive_sum": float(den[den > 0].min()) if np.any(den > 0) else None}
+
+
 def run_precision(args):
     """Precision study: the 2048x1024x64 rotation grid with blobs on a 1e-6
     background, 100 steps, in every arithmetic mode and scheme variant.
@@ -595,6 +662,7 @@ def run_precision(args):
         out, _ = solve(full, next(m for m in PRECISION_MODES if m[0] == name))
         modes[name]["full_vs_f64"] = _errors(out.double().cpu().numpy(), f64_full, background)
         del out
+    beta_study = beta_denominator_study(small, nsteps)
     line = {"metric": METRIC, "value": modes["f32"]["full_2048x1024x64"]["gcell_steps_per_s"],
             "unit": UNIT, "n_gpus": 1, "steps": 1, "warmup": 1, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -606,7 +674,7 @@ def run_precision(args):
                        "background_threshold": background},
             "oracle": {"what": what, "threads": threads, "seconds": t_oracle,
                        "mass_drift": oracle_mass},
-            "modes": modes}
+            "modes": modes, "beta_denominators": beta_study}
     print(json.dumps(line), flush=True)
     return 0
 
