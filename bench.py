@@ -23,6 +23,10 @@ Prints ONE JSON line (rank 0):
 sample per step.  Under torchrun (N > 1) every rank runs its own replica of
 the problem (the workload does not shard across GPUs here).
 
+  arms       config 2's comparison arms, each timed in the same process
+  workloads  short runs of the 64-grid tracer batch (10 steps) and of the
+             serving loop (Poisson arrivals at 200 req/s for 10 s)
+
 Other workloads (--workload): tracers (64 uneven grids in one batched
 launch), serve (Poisson arrivals through the serving runtime) and precision
 (FP32 / FP32 with FP64 limiter sums / FP64, three passes and the
@@ -72,6 +76,8 @@ def parse():
     ap.add_argument("--no-clocks", action="store_true")
     ap.add_argument("--no-arms", action="store_true",
                     help="skip the comparison arms (stage path, one tile height, batched splits)")
+    ap.add_argument("--no-workloads", action="store_true",
+                    help="skip the short tracer-batch and serving runs added to the default line")
     ap.add_argument("--workload", default="grid", choices=["grid", "tracers", "serve", "precision"],
                     help="grid: 1024x512x64 (default); tracers: 64 uneven grids batched; "
                          "serve: Poisson arrivals through the serving runtime vs one solve per launch; "
@@ -299,7 +305,7 @@ def run_reference(args, rank, world):
     return 0
 
 
-def run_tracers(args):
+def tracers_line(warmup, steps, per_grid_tiles=True):
     """64 independent tracer grids (nx, ny log-uniform in [32, 512], nz in
     [16, 64], constant Courant vectors), 20 steps each: one persistent,
     graph-captured batched launch per step vs one launch per grid."""
@@ -324,16 +330,16 @@ def run_tracers(args):
                 for var in range(mp.Batch.VARIANTS):
                     if b.work(var)[0]:
                         b.set_balanced_split(var, nsm)
-            for _ in range(args.warmup):
+            for _ in range(warmup):
                 b.step(nsteps, graph=True)
             torch.cuda.synchronize()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            for _ in range(args.steps):
+            for _ in range(steps):
                 b.step(nsteps, graph=True)
             e1.record(stream)
             torch.cuda.synchronize()
-            return e0.elapsed_time(e1) / args.steps
+            return e0.elapsed_time(e1) / steps
 
     nsm = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
     every = list(range(len(fs)))
@@ -344,32 +350,34 @@ def run_tracers(args):
     from paper_1507_01265_gb300 import tune
     pairs = every
     rates = {}
-    for ty in (24, 16, 28):
-        ms = time_batch(pairs, tile=(32, ty))
-        work = sum(math.ceil(fs[i].nx / 32) * math.ceil(fs[i].ny / ty) * 32 * ty * (fs[i].nz + 3)
-                   for i in pairs)
-        rates[ty] = work * nsteps / (ms * 1e-3)
-    chosen = dict(zip(pairs, tune.choose_tiles([(fs[i].nx, fs[i].ny, fs[i].nz) for i in pairs], rates, nsm)))
-    tiles = [chosen.get(i, 0) for i in every]
-    res["per_grid_tiles"] = time_batch(every, tiles=tiles)
+    chosen = {}
+    if per_grid_tiles:
+        for ty in (24, 16, 28):
+            ms = time_batch(pairs, tile=(32, ty))
+            work = sum(math.ceil(fs[i].nx / 32) * math.ceil(fs[i].ny / ty) * 32 * ty * (fs[i].nz + 3)
+                       for i in pairs)
+            rates[ty] = work * nsteps / (ms * 1e-3)
+        chosen = dict(zip(pairs, tune.choose_tiles([(fs[i].nx, fs[i].ny, fs[i].nz) for i in pairs], rates, nsm)))
+        tiles = [chosen.get(i, 0) for i in every]
+        res["per_grid_tiles"] = time_batch(every, tiles=tiles)
     solvers = [mp.Solver(f.nx, f.ny, f.nz, periodic=f.periodic) for f in fs]
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         for s_, t in zip(solvers, ts):
             s_.step(*t, nsteps)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    for _ in range(args.steps):
+    for _ in range(steps):
         for s_, t in zip(solvers, ts):
             s_.step(*t, nsteps)
     e1.record(stream)
     torch.cuda.synchronize()
-    res["per_grid"] = e0.elapsed_time(e1) / args.steps
+    res["per_grid"] = e0.elapsed_time(e1) / steps
     for s_ in solvers:
         s_.close()
     v = cells * nsteps / (res["batched"] * 1e-3) / 1e9
-    line = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": res["batched"], "higher_is_better": True,
+    line = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": 1, "steps": steps,
+            "warmup": warmup, "ms_per_step": res["batched"], "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "64 tracer grids, nx/ny log-uniform [32,512], nz [16,64], 20 steps; "
                                    "batched launch (one CTA per tile, largest first) captured in a CUDA graph",
@@ -379,12 +387,17 @@ def run_tracers(args):
             "speedup_vs_per_grid": res["per_grid"] / res["batched"],
             "persistent_balanced_split": {"value": cells * nsteps / (res["batched_persistent"] * 1e-3) / 1e9,
                                           "ms_per_step": res["batched_persistent"]},
-            "per_grid_tiles": {"value": cells * nsteps / (res["per_grid_tiles"] * 1e-3) / 1e9,
-                               "ms_per_step": res["per_grid_tiles"],
-                               "grids": len(pairs),
-                               "tile_y_counts": {str(ty): sum(1 for i in pairs if chosen[i] == ty)
-                                                 for ty in (24, 16, 28)},
-                               "rates_cell_planes_per_s": {str(k): v for k, v in rates.items()}}}
+            "per_grid_tiles": None if not per_grid_tiles else {
+                "value": cells * nsteps / (res["per_grid_tiles"] * 1e-3) / 1e9,
+                "ms_per_step": res["per_grid_tiles"],
+                "grids": len(pairs),
+                "tile_y_counts": {str(ty): sum(1 for i in pairs if chosen[i] == ty) for ty in (24, 16, 28)},
+                "rates_cell_planes_per_s": {str(k): v for k, v in rates.items()}}}
+    return line
+
+
+def run_tracers(args):
+    line = tracers_line(args.warmup, args.steps)
     print(json.dumps(line), flush=True)
     return 0
 
@@ -412,14 +425,14 @@ def serve_requests(rate, seconds, seed=1511):
     return templates, reqs
 
 
-def run_serve(args):
+def serve_line(rate, seconds):
     """Served (continuous batching) vs plain (one solve per launch, in arrival
     order): throughput and p50/p99 latency under the same arrivals."""
     import threading
     import numpy as np
     import torch
     import paper_1507_01265_gb300 as mp
-    templates, reqs = serve_requests(args.serve_rate, args.serve_seconds)
+    templates, reqs = serve_requests(rate, seconds)
     pin = lambda a: torch.from_numpy(a).pin_memory()
     tmpl = [(pin(f.h), f.psi, pin(f.u1), pin(f.u2), pin(f.u3)) for f in templates]
     outs = [pin(templates[k].psi.copy()) for _, k, _ in reqs]
@@ -486,10 +499,15 @@ def run_serve(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "serving: Poisson arrivals %.0f req/s for %.0f s, dims log-uniform "
                                    "32^3..512x256x64, nsteps U[10,200], 120 GB budget"
-                                   % (args.serve_rate, args.serve_seconds),
-                       "offered_gcell_steps_per_s": work / args.serve_seconds / 1e9},
+                                   % (rate, seconds),
+                       "offered_gcell_steps_per_s": work / seconds / 1e9},
             "served": served, "plain_one_solve_per_launch": plain,
             "throughput_ratio": served["gcell_steps_per_s"] / plain["gcell_steps_per_s"]}
+    return line
+
+
+def run_serve(args):
+    line = serve_line(args.serve_rate, args.serve_seconds)
     print(json.dumps(line), flush=True)
     return 0
 
@@ -797,6 +815,21 @@ def main():
                "serial": {"value": world * ncells * NSTEPS * args.e2e_steps / dt_serial / 1e9,
                           "api": "mpdata_solve_host"}}
 
+    # short runs of the batched and served workloads (configs 3 and 4), outside
+    # the timed region, so that one bench run records every workload
+    workloads = None
+    if world == 1 and args.path == "fused" and tile is None and not args.no_workloads:
+        tr = tracers_line(3, 10, per_grid_tiles=False)
+        sv = serve_line(200.0, 10.0)
+        workloads = {
+            "tracers_64_grids": {k: tr[k] for k in ("value", "unit", "ms_per_step", "per_grid_launches",
+                                                    "speedup_vs_per_grid", "persistent_balanced_split")},
+            "serve_200rps_10s": {k: sv[k] for k in ("served", "plain_one_solve_per_launch", "throughput_ratio")},
+        }
+        workloads["tracers_64_grids"]["workload"] = tr["config"]["workload"]
+        workloads["serve_200rps_10s"]["workload"] = sv["config"]["workload"]
+        workloads["serve_200rps_10s"]["offered_gcell_steps_per_s"] = sv["config"]["offered_gcell_steps_per_s"]
+
     if rank == 0:
         cpu = None if args.no_cpu_baseline else oracle_sample()
         line = {
@@ -807,7 +840,7 @@ def main():
                            l2="inputs 671 MB + output 134 MB per step > 129 MB L2 (no flush)",
                            parallelism="replicas" if world > 1 else "single"),
             "roofline": roofline, "e2e": e2e, "cpu_baseline": cpu,
-            "clocks": clocks, "gpu_launches": launches, "arms": arms,
+            "clocks": clocks, "gpu_launches": launches, "arms": arms, "workloads": workloads,
             "pct_hbm_roofline": 100.0 * roofline["frac"],
             "ci95_pct": ci95_pct(per_solve),
         }
