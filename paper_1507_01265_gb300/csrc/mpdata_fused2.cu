@@ -100,20 +100,31 @@ __device__ __forceinline__ F2 pseudo_velocity(F2 U, F2 pR, F2 pL, F2 psum, F2 sp
     return sub(mul(sub(fabs2(U), mul(U, t)), A), mul(t8, fma2(ua, Ba, mul(ub, Bb))));
 }
 
+// Shared-memory planes: rows of EXL = TX + 8 loaded columns at a pitch of
+// EX = EXL + 4 words.  The halo threads of the onion order include two
+// vertical strips (one column pair, consecutive rows in consecutive lanes);
+// with a pitch of 40 words (8 mod 32) a strip's 32 lanes fall on 4 bank
+// positions, with 44 (12 mod 32) on 8, which halves the wavefronts of every
+// strip access.  The pitch stays a multiple of 4 words so that rows stay
+// 16-byte aligned for the 16-byte cp.async (a pitch of 42 would spread the
+// strips over 16 positions but needs 8-byte copies, which go through L1 and
+// evict the kernel's spill lines).
 template <int TX, int TY, int NR_ = 5>
 struct Lay2 {
     static_assert(TX % 4 == 0, "TX must be a multiple of 4");
     static constexpr int HX = TX / 2;           // output pairs per row
     static constexpr int NPX = HX + 2;          // pairs of the radius-2 regions
-    static constexpr int EX = TX + 8;           // plane row: columns -4 .. TX+3
+    static constexpr int EXL = TX + 8;          // loaded plane row: columns -4 .. TX+3
+    static constexpr int EX = EXL + 4;          // row pitch (words)
     static constexpr int EY = TY + 6;           // plane rows: -3 .. TY+2
     static constexpr int PL = EX * EY;
+    static constexpr int PLL = EXL * EY;        // loaded elements per plane
     static constexpr int NT = NPX * (TY + 4);   // psi1 region = threads
     static constexpr int N_OUT = HX * TY;
     static constexpr int N_VM = (HX + 1) * (TY + 1);
     static constexpr int N_BETA = NPX * (TY + 2);
     static constexpr int N_V = NPX * (TY + 3);
-    static constexpr int CPR = EX / 4;          // 16-byte chunks per plane row
+    static constexpr int CPR = EXL / 4;         // 16-byte chunks per plane row
     static constexpr int NCH = CPR * EY;
     static_assert(NCH <= NT, "one load chunk per thread");
     static constexpr int NR = NR_;              // input ring depth (planes)
@@ -215,7 +226,7 @@ __device__ __forceinline__ void pairs_tile(const TileArgs &a, int tile, float *s
     const float *__restrict__ u3 = a.u3;
     float *__restrict__ out = a.out;
     const int ntx = a.ntx;
-    constexpr int EX = L::EX, PL = L::PL;
+    constexpr int EX = L::EX, EXL = L::EXL, PL = L::PL, PLL = L::PLL;
     constexpr int PB = PL * 4;         // bytes per plane
     constexpr int FB = L::NR * PB;     // bytes between ring fields
     constexpr int RB = EX * 4;         // bytes per plane row
@@ -263,12 +274,13 @@ __device__ __forceinline__ void pairs_tile(const TileArgs &a, int tile, float *s
     // nx % 4 == 0: one 16-byte chunk (4 columns of one row) per thread and
     // field.  Any other nx: 4-byte copies of plane elements t, t + NT, ...,
     // so that a warp reads 128 contiguous bytes and writes consecutive words.
-    constexpr int NE = (PL + L::NT - 1) / L::NT;
+    constexpr int NE = (PLL + L::NT - 1) / L::NT;
     const bool has_chunk = t < L::NCH;
     int ld_off = 0;
     bool z_all = false, z_u2 = false, patch_u1 = false;
     unsigned ld_dst = 0;
     int e_off[NE];
+    unsigned e_dst[NE];  // shared word offset of each element (rows of pitch EX)
     unsigned e_flags = 0;
     if (a16) {
         if (has_chunk) {
@@ -289,8 +301,10 @@ __device__ __forceinline__ void pairs_tile(const TileArgs &a, int tile, float *s
         for (int r = 0; r < NE; ++r) {
             const int idx = t + r * L::NT;
             e_off[r] = 0;
-            if (idx < PL) {
-                const int lx = x0 - 4 + idx % EX, ly = y0 - 3 + idx / EX;
+            e_dst[r] = 0;
+            if (idx < PLL) {
+                const int lx = x0 - 4 + idx % EXL, ly = y0 - 3 + idx / EXL;
+                e_dst[r] = (unsigned)((idx / EXL) * EX + idx % EXL);
                 int cx, cy;
                 bool outx = false, outy = false;
                 if (perx) cx = wrap(lx, nx); else { outx = lx < 0 || lx >= nx; cx = outx ? 0 : lx; }
@@ -312,6 +326,7 @@ __device__ __forceinline__ void pairs_tile(const TileArgs &a, int tile, float *s
                 const long long pc = pz * nxy + ld_off;
                 const bool zz = E && !perz && (p <= 0 || p >= nz);
                 const unsigned d = ld_dst + so;
+                static_assert(EX % 4 == 0, "rows must stay 16-byte aligned");
                 cp16(d, psi + pc, z_all);
                 cp16(d + FB, u1 + pc, z_all);
                 cp16(d + 2 * FB, u2 + pc, z_u2);
@@ -321,12 +336,12 @@ __device__ __forceinline__ void pairs_tile(const TileArgs &a, int tile, float *s
         } else {
             const long long pz = (E ? (long long)(perz ? wrap(p, nz) : min(max(p, 0), nz - 1)) : (long long)p) * nxy;
             const bool zz = E && !perz && (p <= 0 || p >= nz);
-            const unsigned d0 = sm_base + (unsigned)(t * 4) + so;
+            const unsigned d0 = sm_base + so;
 #pragma unroll
             for (int r = 0; r < NE; ++r) {
-                if (t + r * L::NT < PL) {
+                if (t + r * L::NT < PLL) {
                     const long long o = pz + e_off[r];
-                    const unsigned d = d0 + (unsigned)(r * L::NT * 4);
+                    const unsigned d = d0 + e_dst[r] * 4u;
                     const bool ze = (e_flags >> (3 * r)) & 1u;
                     cp4(d, psi + o, ze);
                     cp4(d + FB, u1 + o, ze || ((e_flags >> (3 * r + 2)) & 1u));
