@@ -134,18 +134,22 @@ struct Lay2 {
 };
 
 // Pair (px, row) of thread t; pair px covers columns 2px-4, 2px-3 of the tile.
-// Rings outwards: out | col-pair HX+2 rows [0,TY], row TY | col-pair 1 rows
-// [-1,TY], row -1 | row TY+1 | row -2.
+// Rings outwards, each stage's region a prefix of t:
+//   out (HX x TY) | N_VM: row TY, col-pair HX+2 rows [0,TY] |
+//   N_BETA: col-pair 1 rows [-1,TY], row -1 | N_V: row TY+1 | NT: row -2.
+// Within a ring the row comes before the strip in N_VM and after it in
+// N_BETA, so that no warp holds more than 19 lanes of a vertical strip (whose
+// lanes are one row pitch apart and share 8 bank positions).
 template <int TX, int TY>
 __device__ __forceinline__ void onion2(int t, int &px, int &ry) {
     using L = Lay2<TX, TY>;
     constexpr int HX = L::HX;
     if (t < L::N_OUT) { px = 2 + t % HX; ry = t / HX; return; }
     t -= L::N_OUT;
-    if (t < TY + 1) { px = HX + 2; ry = t; return; }
-    t -= TY + 1;
     if (t < HX) { px = 2 + t; ry = TY; return; }
     t -= HX;
+    if (t < TY + 1) { px = HX + 2; ry = t; return; }
+    t -= TY + 1;
     if (t < TY + 2) { px = 1; ry = t - 1; return; }
     t -= TY + 2;
     if (t < HX + 1) { px = 2 + t; ry = -1; return; }
