@@ -5,7 +5,7 @@ import math
 
 import pytest
 
-T28, T24 = 2.17, 1.80  # us per plane of one CTA: 32x28 two-column, 32x24 warp-specialised
+T28, T24 = 2.12, 1.76  # us per plane of one CTA: 32x28 two-column, 32x24 warp-specialised
 
 
 def handout(costs, nsm):
