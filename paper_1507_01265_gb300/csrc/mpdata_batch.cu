@@ -12,14 +12,17 @@
 // nearly equal cost) and any other split, including the uneven ones of the
 // speed-function autotuner, can be installed instead.  A step of the batch is
 // one launch per variant; nsteps steps can be captured once into a CUDA graph
-// and replayed.  Each tile is computed by the same code whichever CTA runs
-// it, so every grid's result is bit-identical to the single-grid launch.
+// and replayed.  32x24 tiles of grids with nx % 4 == 0 run the
+// warp-specialised kernel, as a single-grid launch with that tile does.  Each
+// tile is computed by the same code whichever CTA runs it, so every grid's
+// result is bit-identical to the single-grid launch.
 #include <stdarg.h>
 #include <stdio.h>
 #include <string.h>
 
 #include <algorithm>
 #include <map>
+#include <memory>
 #include <new>
 #include <string>
 #include <vector>
@@ -32,22 +35,24 @@ using mpdata::Grid;
 namespace {
 
 enum Variant {
-    kPairs24Periodic = 0,  // two columns per thread, tile 32x24, x and y periodic
+    kPairs24Periodic = 0,  // two columns per thread, tile 32x24, x and y periodic (nx % 4 != 0)
     kPairs24Lid = 1,       // same with a lid on x or y
-    kSingle = 2,           // reserved (no FP32 grid needs the one-column kernel)
+    kWs24Periodic = 2,     // warp-specialised tile 32x24, x and y periodic (nx % 4 == 0)
     kPairs16Periodic = 3,  // two columns per thread, tile 32x16
     kPairs16Lid = 4,
     kPairs28Periodic = 5,  // two columns per thread, tile 32x28
     kPairs28Lid = 6,
-    kNumVariants = 7
+    kWs24Lid = 7,          // warp-specialised tile 32x24 with a lid on x or y (nx % 4 == 0)
+    kNumVariants = 8
 };
 
 int variant_tile_y(int v) {
-    if (v == kPairs24Periodic || v == kPairs24Lid) return 24;
+    if (v == kPairs24Periodic || v == kPairs24Lid || v == kWs24Periodic || v == kWs24Lid) return 24;
     if (v == kPairs28Periodic || v == kPairs28Lid) return 28;
     return 16;
 }
-bool variant_lid(int v) { return v == kPairs24Lid || v == kPairs16Lid || v == kPairs28Lid; }
+bool variant_lid(int v) { return v == kPairs24Lid || v == kPairs16Lid || v == kPairs28Lid || v == kWs24Lid; }
+bool variant_ws(int v) { return v == kWs24Periodic || v == kWs24Lid; }
 
 struct Group {
     std::vector<int2> items;  // (grid, tile), by decreasing cost
@@ -142,7 +147,39 @@ int upload_group(mpdata_batch *b, int v) {
     return MPDATA_OK;
 }
 
+// The direct form of a variant's launch (grid table in the kernel
+// parameters): only for the default split (one CTA per item, in order) and
+// at most kDirectMaxRuns runs of consecutive tiles of one grid.  Returns
+// false when the variant needs the general kernel.
+bool build_direct(const mpdata_batch *b, const Group &G, mpdata::DirectBatch &d) {
+    const int n = (int)G.items.size();
+    if (G.ncta != n || (int)G.begin.size() != n + 1) return false;
+    for (int i = 0; i <= n; ++i)
+        if (G.begin[i] != i) return false;
+    d.nruns = 0;
+    for (int i = 0; i < n; ++i) {
+        const int2 w = G.items[i];
+        const bool extend = d.nruns > 0 && G.items[i - 1].x == w.x && G.items[i - 1].y + 1 == w.y;
+        if (extend) continue;
+        if (d.nruns == mpdata::kDirectMaxRuns) return false;
+        d.start[d.nruns] = i;
+        d.tile0[d.nruns] = w.y;
+        d.g[d.nruns] = b->grids[w.x];
+        ++d.nruns;
+    }
+    d.start[d.nruns] = n;
+    return d.nruns > 0;
+}
+
 int enqueue_steps(mpdata_batch *b, int nsteps, cudaStream_t s) {
+    // direct-launch tables of the variants that can use them (host memory;
+    // a launch copies its parameters)
+    std::vector<std::unique_ptr<mpdata::DirectBatch>> direct(kNumVariants);
+    for (int v = 0; v < kNumVariants; ++v) {
+        if (b->group[v].items.empty()) continue;
+        direct[v].reset(new (std::nothrow) mpdata::DirectBatch);
+        if (direct[v] && !build_direct(b, b->group[v], *direct[v])) direct[v].reset();
+    }
     if (nsteps & 1) {
         for (int i = 0; i < b->ngrids; ++i) {
             cudaError_t e = cudaMemcpyAsync(b->grids[i].buf[1], b->grids[i].buf[0], b->bytes[i],
@@ -155,9 +192,18 @@ int enqueue_steps(mpdata_batch *b, int nsteps, cudaStream_t s) {
         for (int v = 0; v < kNumVariants; ++v) {
             Group &G = b->group[v];
             if (G.items.empty()) continue;
-            const cudaError_t e = mpdata::launch_fused_pairs_batch(
-                32, variant_tile_y(v), b->opts.nonoscillatory, variant_lid(v), b->d_grids, G.d_items,
-                G.d_begin, G.ncta, parity, s);
+            const int nonosc = b->opts.nonoscillatory, lid = variant_lid(v);
+            cudaError_t e;
+            if (direct[v])
+                e = variant_ws(v) ? mpdata::launch_fused_ws_direct(nonosc, lid, *direct[v], parity, s)
+                                  : mpdata::launch_fused_pairs_direct(variant_tile_y(v), nonosc, lid,
+                                                                      *direct[v], parity, s);
+            else
+                e = variant_ws(v) ? mpdata::launch_fused_ws_batch(nonosc, lid, b->d_grids, G.d_items,
+                                                                  G.d_begin, G.ncta, parity, s)
+                                  : mpdata::launch_fused_pairs_batch(32, variant_tile_y(v), nonosc, lid,
+                                                                     b->d_grids, G.d_items, G.d_begin,
+                                                                     G.ncta, parity, s);
             if (e != cudaSuccess) return bcuda(e, "batched kernel launch");
         }
     }
@@ -223,7 +269,9 @@ int mpdata_batch_create_tiles(int ngrids, const int *dims, const int *periodic, 
         g.eps = (float)o.eps;
         const int ty = (tile_y && tile_y[i]) ? tile_y[i] : ty_default;
         const bool lid = !g.g.per[0] || !g.g.per[1];
-        const int v = ty == 24 ? (lid ? kPairs24Lid : kPairs24Periodic)
+        const bool ws = ty == 24 && nx % 4 == 0;
+        const int v = ws ? (lid ? kWs24Lid : kWs24Periodic)
+                      : ty == 24 ? (lid ? kPairs24Lid : kPairs24Periodic)
                       : ty == 28 ? (lid ? kPairs28Lid : kPairs28Periodic)
                                  : (lid ? kPairs16Lid : kPairs16Periodic);
         g.ntx = (nx + tx - 1) / tx;

@@ -573,12 +573,18 @@ __device__ __forceinline__ void pairs_tile(const TileArgs &a, int tile, float *s
 // producers (64) to the consumers (104); the block's total is unchanged
 // (20 x 32 x 96 = 16 x 32 x 104 + 4 x 32 x 64) and every SM sub-partition
 // holds 4 x 32 x 104 + 32 x 64 of its 16 K.  Same arithmetic, operation for
-// operation, as pairs_tile, so the result is bit-identical.
+// operation, as pairs_tile, so the result is bit-identical.  ws_tile with
+// ROLE 2 runs one tile with both roles and moves the registers itself, after
+// the set-up both share; ROLE 0 (producers, threads 512..639) or 1
+// (consumers, 0..511) runs one role of one tile, for a kernel that moves the
+// registers once and loops over tiles (the roles run the same number of
+// planes, so their CTA barriers pair up, and no shared memory is read after a
+// tile's last one).
 __device__ __forceinline__ void named_sync(int id, int count) {
     asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
 }
 
-template <bool NONOSC, bool LID>
+template <bool NONOSC, bool LID, int ROLE>
 __device__ __forceinline__ void ws_tile(const TileArgs &a, int tile, float *sm) {
     constexpr int TX = 32, TY = 24;
     using L = Lay2<TX, TY>;
@@ -620,9 +626,9 @@ __device__ __forceinline__ void ws_tile(const TileArgs &a, int tile, float *sm) 
         return r < 0 ? r + 3 : r;
     };
 
-    if (t >= NC) {
+    if (ROLE == 0 || (ROLE == 2 && t >= NC)) {
         // ================= producers =================
-        asm volatile("setmaxnreg.dec.sync.aligned.u32 64;\n" ::: "memory");
+        if constexpr (ROLE == 2) asm volatile("setmaxnreg.dec.sync.aligned.u32 64;\n" ::: "memory");
         const int j = t - NC;
         int ld_off[3];
         unsigned ld_dst[3];
@@ -764,7 +770,7 @@ __device__ __forceinline__ void ws_tile(const TileArgs &a, int tile, float *sm) 
     }
 
     // ================= consumers =================
-    asm volatile("setmaxnreg.inc.sync.aligned.u32 104;\n" ::: "memory");
+    if constexpr (ROLE == 2) asm volatile("setmaxnreg.inc.sync.aligned.u32 104;\n" ::: "memory");
     const bool in_t = t < L::NT;
     int px = 1, ry = -2;
     if (in_t) onion2<TX, TY>(t, px, ry);
@@ -943,7 +949,30 @@ __device__ __forceinline__ void ws_tile(const TileArgs &a, int tile, float *sm) 
 template <bool NONOSC, bool LID>
 __global__ void __launch_bounds__(640, 1) k_fused_ws(TileArgs a) {
     extern __shared__ __align__(16) float sm[];
-    ws_tile<NONOSC, LID>(a, blockIdx.x, sm);
+    ws_tile<NONOSC, LID, 2>(a, blockIdx.x, sm);
+}
+
+// Batched form: CTA c runs the 32x24 tiles [begin[c], begin[c+1]) of the item
+// list (grids with nx % 4 == 0), each role looping over them.
+template <bool NONOSC, bool LID>
+__global__ void __launch_bounds__(640, 1)
+    k_fused_ws_batch(const BatchGrid *__restrict__ grids, const int2 *__restrict__ items,
+                     const int *__restrict__ begin, int parity) {
+    extern __shared__ __align__(16) float sm[];
+    const int lo = begin[blockIdx.x], hi = begin[blockIdx.x + 1];
+    if (threadIdx.x >= 512) {
+        asm volatile("setmaxnreg.dec.sync.aligned.u32 64;\n" ::: "memory");
+        for (int it = lo; it < hi; ++it) {
+            const int2 w = items[it];
+            ws_tile<NONOSC, LID, 0>(batch_args(grids[w.x], parity), w.y, sm);
+        }
+    } else {
+        asm volatile("setmaxnreg.inc.sync.aligned.u32 104;\n" ::: "memory");
+        for (int it = lo; it < hi; ++it) {
+            const int2 w = items[it];
+            ws_tile<NONOSC, LID, 1>(batch_args(grids[w.x], parity), w.y, sm);
+        }
+    }
 }
 
 template <int TX, int TY, bool NONOSC, bool LID, int AL>
@@ -965,6 +994,33 @@ __global__ void __launch_bounds__(Lay2<TX, TY>::NT, 1)
         const int2 w = items[it];
         pairs_tile<TX, TY, NONOSC, LID, 2>(batch_args(grids[w.x], parity), w.y, sm);
     }
+}
+
+// Run of CTA c in a direct batch (uniform: every index is blockIdx-derived
+// and every table sits in the parameter space).
+__device__ __forceinline__ int direct_run(const DirectBatch &d, int c) {
+    int lo = 0, hi = d.nruns;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (d.start[mid] <= c) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+template <int TX, int TY, bool NONOSC, bool LID>
+__global__ void __launch_bounds__(Lay2<TX, TY>::NT, 1)
+    k_fused_pairs_direct(const __grid_constant__ DirectBatch d, int parity) {
+    extern __shared__ __align__(16) float sm[];
+    const int c = blockIdx.x, r = direct_run(d, c);
+    pairs_tile<TX, TY, NONOSC, LID, 2>(batch_args(d.g[r], parity), d.tile0[r] + c - d.start[r], sm);
+}
+
+template <bool NONOSC, bool LID>
+__global__ void __launch_bounds__(640, 1) k_fused_ws_direct(const __grid_constant__ DirectBatch d, int parity) {
+    extern __shared__ __align__(16) float sm[];
+    const int c = blockIdx.x, r = direct_run(d, c);
+    ws_tile<NONOSC, LID, 2>(batch_args(d.g[r], parity), d.tile0[r] + c - d.start[r], sm);
 }
 
 template <int TX, int TY>
@@ -1071,6 +1127,51 @@ cudaError_t launch_fused_bands(const Grid &g, int nonosc, double eps, const Band
     e = cudaEventRecord(ev_join, s2);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ev_join, 0);
     return e;
+}
+
+cudaError_t launch_fused_ws_batch(int nonosc, int lid, const BatchGrid *grids, const int2 *items,
+                                  const int *begin, int ncta, int parity, cudaStream_t s) {
+    using L = Lay2<32, 24>;
+    const size_t smem = (size_t)39 * L::PL * sizeof(float);
+    auto kern = nonosc ? (lid ? k_fused_ws_batch<true, true> : k_fused_ws_batch<true, false>)
+                       : (lid ? k_fused_ws_batch<false, true> : k_fused_ws_batch<false, false>);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<ncta, 640, smem, s>>>(grids, items, begin, parity);
+    return cudaGetLastError();
+}
+
+template <int TX, int TY>
+cudaError_t launch_pairs_direct(int nonosc, int lid, const DirectBatch &d, int parity, cudaStream_t s) {
+    using L = Lay2<TX, TY, 4>;
+    const size_t smem = (size_t)L::NPLANES * L::PL * sizeof(float);
+    auto kern = nonosc ? (lid ? k_fused_pairs_direct<TX, TY, true, true> : k_fused_pairs_direct<TX, TY, true, false>)
+                       : (lid ? k_fused_pairs_direct<TX, TY, false, true> : k_fused_pairs_direct<TX, TY, false, false>);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<d.start[d.nruns], L::NT, smem, s>>>(d, parity);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fused_pairs_direct(int ty, int nonosc, int lid, const DirectBatch &d, int parity,
+                                      cudaStream_t s) {
+    if (d.nruns < 1 || d.nruns > kDirectMaxRuns || d.start[d.nruns] < 1) return cudaErrorInvalidValue;
+    if (ty == 16) return launch_pairs_direct<32, 16>(nonosc, lid, d, parity, s);
+    if (ty == 24) return launch_pairs_direct<32, 24>(nonosc, lid, d, parity, s);
+    if (ty == 28) return launch_pairs_direct<32, 28>(nonosc, lid, d, parity, s);
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_fused_ws_direct(int nonosc, int lid, const DirectBatch &d, int parity, cudaStream_t s) {
+    if (d.nruns < 1 || d.nruns > kDirectMaxRuns || d.start[d.nruns] < 1) return cudaErrorInvalidValue;
+    using L = Lay2<32, 24>;
+    const size_t smem = (size_t)39 * L::PL * sizeof(float);
+    auto kern = nonosc ? (lid ? k_fused_ws_direct<true, true> : k_fused_ws_direct<true, false>)
+                       : (lid ? k_fused_ws_direct<false, true> : k_fused_ws_direct<false, false>);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<d.start[d.nruns], 640, smem, s>>>(d, parity);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_fused_pairs_batch(int tx, int ty, int nonosc, int lid, const BatchGrid *grids,

@@ -63,6 +63,21 @@ __host__ __device__ inline TileArgs batch_args(const BatchGrid &b, int parity) {
     return a;
 }
 
+// A batched launch with one CTA per work item, its grid table passed in the
+// kernel parameters (constant bank) instead of global memory: the items form
+// runs of consecutive tiles of one grid, CTA c belongs to the run r with
+// start[r] <= c < start[r+1] and runs tile tile0[r] + c - start[r] of grid
+// g[r].  A CTA's arguments are then uniform across its threads, as in a
+// single-grid launch.  At most kDirectMaxRuns runs (about 28 KB of
+// parameters, within the 32 KB limit).
+constexpr int kDirectMaxRuns = 320;
+struct DirectBatch {
+    int nruns;
+    int start[kDirectMaxRuns + 1];
+    int tile0[kDirectMaxRuns];
+    BatchGrid g[kDirectMaxRuns];
+};
+
 // Launchers of the stage-per-kernel path (mpdata_stages.cu).
 // Intermediates of the stage path; psi2 and w1..w3 (the second corrective
 // pass's pseudo-velocities) only with three passes.
@@ -92,6 +107,13 @@ bool fused_pairs_supported(const Grid &g, int tile_x, int tile_y);
 cudaError_t launch_fused_pairs_batch(int tile_x, int tile_y, int nonosc, int lid,
                                      const BatchGrid *grids, const int2 *items, const int *begin,
                                      int ncta, int parity, cudaStream_t s);
+// The same with the warp-specialised 32x24 kernel (grids with nx % 4 == 0).
+cudaError_t launch_fused_ws_batch(int nonosc, int lid, const BatchGrid *grids, const int2 *items,
+                                  const int *begin, int ncta, int parity, cudaStream_t s);
+// One CTA per item, grid table in the parameters (d.start[d.nruns] CTAs).
+cudaError_t launch_fused_pairs_direct(int tile_y, int nonosc, int lid, const DirectBatch &d, int parity,
+                                      cudaStream_t s);
+cudaError_t launch_fused_ws_direct(int nonosc, int lid, const DirectBatch &d, int parity, cudaStream_t s);
 cudaError_t launch_fused_pairs(const Grid &g, int nonosc, double eps, int tile_x, int tile_y,
                                const void *h, const void *psi, const void *u1, const void *u2,
                                const void *u3, void *out, cudaStream_t s);

@@ -35,6 +35,7 @@
 #include <condition_variable>
 #include <deque>
 #include <mutex>
+#include <memory>
 #include <new>
 #include <thread>
 #include <unordered_map>
@@ -252,11 +253,12 @@ cudaError_t run_tick(mpdata_server *s, const std::vector<Request *> &act, int ch
             cost[r->variant].push_back(32.0 * ty * (r->bg.g.nz + 3));
         }
     }
-    int ncta[kNumVariants];
+    int ncta[kNumVariants], ibase[kNumVariants];
     std::vector<int> begin_all;
     int item_base = 0;
     for (int v = 0; v < kNumVariants; ++v) {
         voff[v] = (int)begin_all.size();
+        ibase[v] = item_base;
         const int n = (int)items[v].size();
         ncta[v] = n;  // one CTA per tile
         if (n) {
@@ -269,21 +271,55 @@ cudaError_t run_tick(mpdata_server *s, const std::vector<Request *> &act, int ch
         item_base += n;
     }
     T.h_begin = begin_all;
-    e = ensure(&T.d_grids, &T.cap_grids, (size_t)na, s->stream);
-    if (e == cudaSuccess) e = ensure(&T.d_items, &T.cap_items, T.h_items.size(), s->stream);
-    if (e == cudaSuccess) e = ensure(&T.d_begin, &T.cap_begin, T.h_begin.size(), s->stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(T.d_grids, T.h_grids.data(), sizeof(BatchGrid) * na, cudaMemcpyHostToDevice, s->stream);
-    if (e == cudaSuccess && !T.h_items.empty())
-        e = cudaMemcpyAsync(T.d_items, T.h_items.data(), sizeof(int2) * T.h_items.size(), cudaMemcpyHostToDevice, s->stream);
-    if (e == cudaSuccess && !T.h_begin.empty())
-        e = cudaMemcpyAsync(T.d_begin, T.h_begin.data(), sizeof(int) * T.h_begin.size(), cudaMemcpyHostToDevice, s->stream);
-    for (int st = 0; st < chunk && e == cudaSuccess; ++st) {
-        const int parity = st & 1;
-        for (int v = 0; v < kNumVariants && e == cudaSuccess; ++v) {
-            if (!ncta[v]) continue;
-            const int *begin = T.d_begin + voff[v];
-            e = mpdata::launch_fused_pairs_batch(32, s->o.tile_y, s->o.nonoscillatory, v == kPairsLid,
-                                                     T.d_grids, T.d_items, begin, ncta[v], parity, s->stream);
+    // Direct launches: each variant's items are runs of consecutive tiles of
+    // one request (all tiles of a request cost the same, so the stable sort
+    // keeps them together); with at most kDirectMaxRuns runs per variant the
+    // grid table travels in the kernel parameters and nothing is uploaded.
+    std::unique_ptr<mpdata::DirectBatch> direct[kNumVariants];
+    bool all_direct = true;
+    for (int v = 0; v < kNumVariants && all_direct; ++v) {
+        if (!ncta[v]) continue;
+        direct[v].reset(new (std::nothrow) mpdata::DirectBatch);
+        mpdata::DirectBatch *d = direct[v].get();
+        if (!d) { all_direct = false; break; }
+        d->nruns = 0;
+        for (int k = 0; k < ncta[v]; ++k) {
+            const int2 w = T.h_items[ibase[v] + k];
+            if (k > 0) {
+                const int2 prev = T.h_items[ibase[v] + k - 1];
+                if (prev.x == w.x && prev.y + 1 == w.y) continue;
+            }
+            if (d->nruns == mpdata::kDirectMaxRuns) { all_direct = false; break; }
+            d->start[d->nruns] = k;
+            d->tile0[d->nruns] = w.y;
+            d->g[d->nruns] = T.h_grids[w.x];
+            ++d->nruns;
+        }
+        d->start[d->nruns] = ncta[v];
+    }
+    if (all_direct) {
+        for (int st = 0; st < chunk && e == cudaSuccess; ++st)
+            for (int v = 0; v < kNumVariants && e == cudaSuccess; ++v)
+                if (ncta[v])
+                    e = mpdata::launch_fused_pairs_direct(s->o.tile_y, s->o.nonoscillatory, v == kPairsLid,
+                                                          *direct[v], st & 1, s->stream);
+    } else {
+        e = ensure(&T.d_grids, &T.cap_grids, (size_t)na, s->stream);
+        if (e == cudaSuccess) e = ensure(&T.d_items, &T.cap_items, T.h_items.size(), s->stream);
+        if (e == cudaSuccess) e = ensure(&T.d_begin, &T.cap_begin, T.h_begin.size(), s->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(T.d_grids, T.h_grids.data(), sizeof(BatchGrid) * na, cudaMemcpyHostToDevice, s->stream);
+        if (e == cudaSuccess && !T.h_items.empty())
+            e = cudaMemcpyAsync(T.d_items, T.h_items.data(), sizeof(int2) * T.h_items.size(), cudaMemcpyHostToDevice, s->stream);
+        if (e == cudaSuccess && !T.h_begin.empty())
+            e = cudaMemcpyAsync(T.d_begin, T.h_begin.data(), sizeof(int) * T.h_begin.size(), cudaMemcpyHostToDevice, s->stream);
+        for (int st = 0; st < chunk && e == cudaSuccess; ++st) {
+            const int parity = st & 1;
+            for (int v = 0; v < kNumVariants && e == cudaSuccess; ++v) {
+                if (!ncta[v]) continue;
+                const int *begin = T.d_begin + voff[v];
+                e = mpdata::launch_fused_pairs_batch(32, s->o.tile_y, s->o.nonoscillatory, v == kPairsLid,
+                                                         T.d_grids, T.d_items, begin, ncta[v], parity, s->stream);
+            }
         }
     }
     if (e == cudaSuccess) e = cudaEventRecord(T.ev, s->stream);

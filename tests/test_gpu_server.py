@@ -185,3 +185,23 @@ def test_destroy_releases_blocked_waiters(mp):
     th.join(timeout=60)
     assert not th.is_alive()
     assert codes == [mp._lib.MPDATA_ECANCELED]
+
+
+def test_more_resident_requests_than_direct_runs(mp):
+    """Ticks normally pass their grid table in the kernel parameters (up to
+    320 requests per kernel variant); with more requests resident the tick
+    uploads the table and runs the general batched kernel.  Either way each
+    result is the request's bits alone."""
+    st = F.Stream(13)
+    fs = []
+    for i in range(360):
+        nx, ny, nz = 8 + 4 * int(st.scalar(0, 3)), 8 + int(st.scalar(0, 5)), 4
+        fs.append(F.rotation_blobs(nx=nx, ny=ny, nz=nz, max_c=0.3, nblobs=1, nsteps=40, seed=500 + i,
+                                   periodic=(1, 1, 0)))
+    outs = [f.psi.copy() for f in fs]
+    with mp.Server(hbm_budget_bytes=256 << 20, max_active=512, chunk_steps=2) as srv:
+        tickets = [srv.submit(f.h, o, f.u1, f.u2, f.u3, f.nsteps, periodic=f.periodic) for f, o in zip(fs, outs)]
+        for t in tickets:
+            srv.wait(t, timeout_ms=120000)
+    for f, o in zip(fs[::7], outs[::7]):
+        assert np.array_equal(o.astype(np.float64), run_gpu(f, f.nsteps, tile=(32, 24))), f.name
