@@ -237,6 +237,23 @@ def tile_times(grids, tiles=TILES, steps=20):
     return rows
 
 
+def per_plane_medians(rows, nsm):
+    """The default-tile model's table: per tile shape, the median of step
+    time / (nz + 6) over the grids that need at most one tile per SM, for
+    nx % 4 == 0 and for other nx."""
+    import statistics
+    out = {}
+    for tile in rows[0]["us"]:
+        tx, ty = (int(v) for v in tile.split("x"))
+        for aligned in (True, False):
+            v = [r["us"][tile] / (r["grid"][2] + 6) for r in rows
+                 if (r["grid"][0] % 4 == 0) == aligned
+                 and math.ceil(r["grid"][0] / tx) * math.ceil(r["grid"][1] / ty) <= nsm]
+            if v:
+                out["%s %s" % (tile, "nx%4==0" if aligned else "other nx")] = statistics.median(v)
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--grid", type=int, nargs=3, default=[1024, 512, 64])
@@ -252,7 +269,8 @@ def main():
         best = sum(min(r["us"].values()) for r in rows)
         dflt = sum(r["us"][r["default"]] for r in rows)
         print(json.dumps({"sum_us_best": best, "sum_us_default": dflt,
-                          "sum_us_by_tile": {k: sum(r["us"][k] for r in rows) for k in rows[0]["us"]}}))
+                          "sum_us_by_tile": {k: sum(r["us"][k] for r in rows) for k in rows[0]["us"]},
+                          "per_plane_us": per_plane_medians(rows, num_sms())}))
         return
     rep = tune_grid(*a.grid, steps=a.steps, xs_max=a.xs_max)
     print(json.dumps(rep))
