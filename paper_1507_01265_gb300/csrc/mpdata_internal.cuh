@@ -77,6 +77,8 @@ struct DirectBatch {
     int tile0[kDirectMaxRuns];
     BatchGrid g[kDirectMaxRuns];
 };
+// kernel parameters are limited to 32764 bytes (with the parity int after it)
+static_assert(sizeof(DirectBatch) + 8 <= 32764, "DirectBatch exceeds the kernel parameter limit");
 
 // Launchers of the stage-per-kernel path (mpdata_stages.cu).
 // Intermediates of the stage path; psi2 and w1..w3 (the second corrective
