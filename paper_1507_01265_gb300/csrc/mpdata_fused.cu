@@ -444,10 +444,10 @@ void fused_default_tile(int dtype, const Grid &g, int nsm, int *tx, int *ty) {
         // runs warp-specialised.  Medians over serving-size grids with at most
         // one tile per SM: step time / (nz + 6)
         {32, 24, 1.76, 1.90},
-        {32, 28, 2.12, 2.46},  // 18 warps at 96 registers: slow alone, fast in full waves
+        {32, 28, 1.96, 2.47},  // 18 compute warps at 96 registers (+2 loader warps when nx % 4 == 0)
         {32, 16, 1.40, 1.47},
-        {24, 16, 1.75, 1.76},  // one-column kernel
-        {16, 16, 1.44, 1.45},
+        {24, 16, 1.76, 1.77},  // one-column kernel
+        {16, 16, 1.46, 1.45},
     };
     const int sms = nsm > 0 ? nsm : 1 << 30;  // unknown device: every grid is one wave
     double best = 0.0;
@@ -491,7 +491,7 @@ bool fused_band_plan(const Grid &g, int nsm, BandPlan *plan) {
     // one tile height would leave a mostly empty band.  Per-plane times as in
     // fused_default_tile; 0.02 x the 28-row plane time covers the fork and the
     // join.
-    const double t28 = 2.12, t24 = 1.76;
+    const double t28 = 1.96, t24 = 1.76;
     if (nsm <= 0 || g.nx % 4 != 0) return false;
     const long long ntx = (g.nx + 31) / 32;
     const long long w24 = (ntx * ((g.ny + 23) / 24) + nsm - 1) / nsm, w28 = (ntx * ((g.ny + 27) / 28) + nsm - 1) / nsm;

@@ -30,7 +30,10 @@
 // each stage's region is a prefix of the thread index.
 // The 32x24 tile of a grid with nx % 4 == 0 runs a warp-specialised form
 // (k_fused_ws): producer warps load and run the donor pass, consumer warps
-// the rest.
+// the rest.  The 32x28 tile of such a grid adds two loader warps to its 18
+// (pairs_loader): they issue and wait for every input load, so the compute
+// threads hold no load state (fewer spills) and no load instructions, and the
+// 20 warps spread 5 to each scheduler.
 #include <type_traits>
 
 #include "mpdata_internal.cuh"
@@ -218,9 +221,96 @@ using IC = std::integral_constant<int, V>;
 using BT = std::integral_constant<bool, true>;
 using BF = std::integral_constant<bool, false>;
 
-template <int TX, int TY, bool NONOSC, bool LID, int AL>
+// Loader warps of the two-column tile (k_fused_pairs with LD): threads NT ..
+// NT + 63 issue every 16-byte input load of the tile and wait for them, on the
+// same schedule and with the same barriers (three per plane and one at the
+// end) as pairs_tile, so that the compute threads carry no load state.
+template <int TX, int TY, bool LID>
+__device__ __forceinline__ void pairs_loader(const TileArgs &a, int tile, float *sm) {
+    using L = Lay2<TX, TY, 4>;
+    constexpr int NLD = 64;
+    constexpr int KCH = (L::NCH + NLD - 1) / NLD;
+    static_assert(KCH <= 8, "chunk flags are packed 8 per byte");
+    constexpr int PL = L::PL, PB = PL * 4, FB = L::NR * PB, EX = L::EX;
+    const Grid &g = a.g;
+    const int nx = g.nx, ny = g.ny, nz = g.nz;
+    const int perx = LID ? g.per[0] : 1, pery = LID ? g.per[1] : 1, perz = g.per[2];
+    const long long nxy = (long long)nx * ny;
+    const int ntx = a.ntx;
+    const int x0 = (tile % ntx) * TX, y0 = a.y0 + (tile / ntx) * TY;
+    const unsigned sm_base = (unsigned)__cvta_generic_to_shared(sm);
+    const int j = threadIdx.x - L::NT;
+    int ld_off[KCH];
+    unsigned ld_dst[KCH];
+    unsigned cfl = 0;  // per chunk k: bit k has, 8+k lid ghost, 16+k y-lid face, 24+k x-lid face
+#pragma unroll
+    for (int k = 0; k < KCH; ++k) {
+        const int c = j + k * NLD;
+        ld_off[k] = 0;
+        ld_dst[k] = 0;
+        if (c < L::NCH) {
+            const int ey = c / L::CPR, cc = c % L::CPR;
+            const int lx = x0 - 4 + 4 * cc, ly = y0 - 3 + ey;
+            int cx, cy;
+            bool outx = false, outy = false;
+            if (perx) cx = wrap(lx, nx); else { outx = lx < 0 || lx >= nx; cx = outx ? 0 : lx; }
+            if (pery) cy = wrap(ly, ny); else { outy = ly < 0 || ly >= ny; cy = outy ? 0 : ly; }
+            const bool za = outx || outy;
+            cfl |= 1u << k;
+            cfl |= (unsigned)za << (8 + k);
+            cfl |= (unsigned)(za || (!pery && ly == 0)) << (16 + k);
+            cfl |= (unsigned)(LID && !perx && lx == 0) << (24 + k);
+            ld_off[k] = cy * nx + cx;
+            ld_dst[k] = sm_base + (unsigned)(ey * EX + 4 * cc) * 4u;
+        }
+    }
+    auto issue = [&](int p, unsigned so) {
+        const long long pz = (long long)(perz ? wrap(p, nz) : min(max(p, 0), nz - 1));
+        const bool zz = !perz && (p <= 0 || p >= nz);
+#pragma unroll
+        for (int k = 0; k < KCH; ++k) {
+            if ((cfl >> k) & 1u) {
+                const long long pc = pz * nxy + ld_off[k];
+                const unsigned d = ld_dst[k] + so;
+                const bool za = (cfl >> (8 + k)) & 1u, zu2 = (cfl >> (16 + k)) & 1u;
+                cp16(d, a.psi + pc, za);
+                cp16(d + FB, a.u1 + pc, za);
+                cp16(d + 2 * FB, a.u2 + pc, zu2);
+                cp16(d + 3 * FB, a.u3 + pc, za || zz);
+                cp16(d + 4 * FB, a.h + pc, za);
+            }
+        }
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
+    };
+    const int p_first = perz ? -3 : -1, p_last = nz + 2;
+    issue(p_first, 0u);
+    issue(p_first + 1, (unsigned)PB);
+#pragma unroll 1
+    for (int p = p_first; p <= p_last; ++p) {
+        const int kk = (p - p_first) & 3;
+        __syncthreads();  // (F)
+        asm volatile("cp.async.wait_group 0;\n" ::: "memory");  // plane p+1 landed
+        if (LID) {
+#pragma unroll
+            for (int k = 0; k < KCH; ++k)
+                if ((cfl >> (24 + k)) & 1u)
+                    sm[(ld_dst[k] - sm_base) / 4u + (unsigned)(L::NR * PL + ((kk + 1) & 3) * PL)] = 0.f;
+        }
+        __syncthreads();  // (H)
+        if (p + 2 <= p_last) issue(p + 2, (unsigned)(((kk + 2) & 3) * PB));
+        __syncthreads();  // (X)
+    }
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
+    __syncthreads();
+}
+
+template <int TX, int TY, bool NONOSC, bool LID, int AL, bool LD = false>
 __device__ __forceinline__ void pairs_tile(const TileArgs &a, int tile, float *sm) {
     using L = Lay2<TX, TY, 4>;
+    static_assert(!LD || AL == 1, "loader warps take the 16-byte loads only");
+    // __syncthreads is an aligned barrier: every warp must reach each one at
+    // one code location, so the loader threads must form whole warps
+    static_assert(!LD || L::NT % 32 == 0, "loader threads must be whole warps");
     const Grid &g = a.g;
     const float eps1 = a.eps;
     const float *__restrict__ h = a.h;
@@ -246,6 +336,12 @@ __device__ __forceinline__ void pairs_tile(const TileArgs &a, int tile, float *s
     const int x0 = (tile % ntx) * TX, y0 = a.y0 + (tile / ntx) * TY;
     const F2 eps = bc(eps1);
 
+    if constexpr (LD) {
+        if (t >= L::NT) {
+            pairs_loader<TX, TY, LID>(a, tile, sm);
+            return;
+        }
+    }
     int px, ry;
     onion2<TX, TY>(t, px, ry);
     const int gx = x0 + 2 * px - 4, gy = y0 + ry;
@@ -279,7 +375,7 @@ __device__ __forceinline__ void pairs_tile(const TileArgs &a, int tile, float *s
     // field.  Any other nx: 4-byte copies of plane elements t, t + NT, ...,
     // so that a warp reads 128 contiguous bytes and writes consecutive words.
     constexpr int NE = (PLL + L::NT - 1) / L::NT;
-    const bool has_chunk = t < L::NCH;
+    const bool has_chunk = !LD && t < L::NCH;
     int ld_off = 0;
     bool z_all = false, z_u2 = false, patch_u1 = false;
     unsigned ld_dst = 0;
@@ -459,11 +555,11 @@ __device__ __forceinline__ void pairs_tile(const TileArgs &a, int tile, float *s
             }
         }
         asm volatile("cp.async.wait_group 0;\n" ::: "memory");  // plane p+1 landed
-        if (LID && patch_u1)
+        if (LID && !LD && patch_u1)
             sm[(ld_dst - sm_base) / 4u + (unsigned)(L::NR * PL + ((kk + 1) & 3) * PL)] = 0.f;
         __syncthreads();  // (H)
         // plane p+2 into the slot of q2, which no stage reads any more
-        if (!E || p + 2 <= p_last) issue(Ec, p + 2, (unsigned)(((kk + 2) & 3) * PB));
+        if (!LD && (!E || p + 2 <= p_last)) issue(Ec, p + 2, (unsigned)(((kk + 2) & 3) * PB));
 
         // ---- gamma ----
         if (in_vm && (!E || (q2 >= 0 && q2 <= nz - 1))) {
@@ -535,8 +631,10 @@ __device__ __forceinline__ void pairs_tile(const TileArgs &a, int tile, float *s
         wlo_v = whi_v; bu_prev = bu_c; bd_prev = bd_c;
     };
 
-    issue(BT(), p_first, 0u);
-    issue(BT(), p_first + 1, (unsigned)PB);
+    if (!LD) {
+        issue(BT(), p_first, 0u);
+        issue(BT(), p_first + 1, (unsigned)PB);
+    }
     const int n_iter = p_last - p_first + 1;
     // interior iterations 3 <= p <= nz - 3, in whole blocks of four starting
     // at an iteration index that is a multiple of four
@@ -975,10 +1073,10 @@ __global__ void __launch_bounds__(640, 1)
     }
 }
 
-template <int TX, int TY, bool NONOSC, bool LID, int AL>
-__global__ void __launch_bounds__(Lay2<TX, TY>::NT, 1) k_fused_pairs(TileArgs a) {
+template <int TX, int TY, bool NONOSC, bool LID, int AL, bool LD = false>
+__global__ void __launch_bounds__(Lay2<TX, TY>::NT + (LD ? 64 : 0), 1) k_fused_pairs(TileArgs a) {
     extern __shared__ __align__(16) float sm[];
-    pairs_tile<TX, TY, NONOSC, LID, AL>(a, blockIdx.x, sm);
+    pairs_tile<TX, TY, NONOSC, LID, AL, LD>(a, blockIdx.x, sm);
 }
 
 // Persistent batched launch: CTA c runs work items [begin[c], begin[c+1]) of
@@ -1038,6 +1136,14 @@ cudaError_t launch_pairs(const Grid &g, int nonosc, double eps, const void *h, c
     else
         kern = nonosc ? (lid ? k_fused_pairs<TX, TY, true, true, 0> : k_fused_pairs<TX, TY, true, false, 0>)
                       : (lid ? k_fused_pairs<TX, TY, false, true, 0> : k_fused_pairs<TX, TY, false, false, 0>);
+    int nthreads = L::NT;
+    if constexpr (TY == 28) {  // two loader warps issue the 16-byte loads (NT is 18 whole warps)
+        if (a16) {
+            kern = nonosc ? (lid ? k_fused_pairs<TX, TY, true, true, 1, true> : k_fused_pairs<TX, TY, true, false, 1, true>)
+                          : (lid ? k_fused_pairs<TX, TY, false, true, 1, true> : k_fused_pairs<TX, TY, false, false, 1, true>);
+            nthreads = L::NT + 64;
+        }
+    }
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     TileArgs a;
@@ -1058,7 +1164,7 @@ cudaError_t launch_pairs(const Grid &g, int nonosc, double eps, const void *h, c
             return cudaGetLastError();
         }
     }
-    kern<<<ntx * nty, L::NT, smem, s>>>(a);
+    kern<<<ntx * nty, nthreads, smem, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -1101,11 +1207,12 @@ cudaError_t launch_fused_bands(const Grid &g, int nonosc, double eps, const Band
     using L24 = Lay2<32, 24>;
     if (g.nx % 4 != 0 || plan.n28 < 1 || plan.n24 < 1) return cudaErrorInvalidValue;
     const bool lid = !g.per[0] || !g.per[1];
-    auto k28 = nonosc ? (lid ? k_fused_pairs<32, 28, true, true, 1> : k_fused_pairs<32, 28, true, false, 1>)
-                      : (lid ? k_fused_pairs<32, 28, false, true, 1> : k_fused_pairs<32, 28, false, false, 1>);
+    auto k28 = nonosc ? (lid ? k_fused_pairs<32, 28, true, true, 1, true> : k_fused_pairs<32, 28, true, false, 1, true>)
+                      : (lid ? k_fused_pairs<32, 28, false, true, 1, true> : k_fused_pairs<32, 28, false, false, 1, true>);
     auto k24 = nonosc ? (lid ? k_fused_ws<true, true> : k_fused_ws<true, false>)
                       : (lid ? k_fused_ws<false, true> : k_fused_ws<false, false>);
     const size_t sm28 = (size_t)L28::NPLANES * L28::PL * sizeof(float);
+    const int nt28 = L28::NT + 64;  // with the two loader warps
     const size_t sm24 = (size_t)39 * L24::PL * sizeof(float);
     cudaError_t e = cudaFuncSetAttribute(k28, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm28);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k24, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm24);
@@ -1119,7 +1226,7 @@ cudaError_t launch_fused_bands(const Grid &g, int nonosc, double eps, const Band
     a.h = (const float *)h; a.psi = (const float *)psi; a.u1 = (const float *)u1;
     a.u2 = (const float *)u2; a.u3 = (const float *)u3; a.out = (float *)out;
     a.y0 = 0;
-    k28<<<a.ntx * plan.n28, L28::NT, sm28, s>>>(a);
+    k28<<<a.ntx * plan.n28, nt28, sm28, s>>>(a);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     a.y0 = 28 * plan.n28;
     k24<<<a.ntx * plan.n24, 640, sm24, s2>>>(a);
