@@ -758,7 +758,7 @@ def main():
     if args.path != "fused":
         kname = "stage kernels"
     elif bands[0]:
-        kname = ("k_fused_pairs<32,28> (rows 0..%d) + k_fused_ws (32x24, rows %d..), concurrent"
+        kname = ("k_fused_pairs<32,28> (rows 0..%d) + k_fused_pairs<32,24> (rows %d..), loader warps, concurrent"
                  % (28 * bands[0] - 1, 28 * bands[0]))
     else:
         kname = "k_fused_pairs"

@@ -260,9 +260,11 @@ int mpdata_mass_noalloc(const void *h, const void *psi, long long n, int dtype, 
  * persistent CTAs.  Each grid has its own tile shape (32x24, 32x16 or
  * 32x28) and runs the kernel a single-grid launch with that tile runs:
  * variant 0 (tile 32x24, x and y periodic, nx % 4 != 0), 1 (32x24, a lid on
- * x or y, nx % 4 != 0), 2 (32x24 warp-specialised, periodic, nx % 4 == 0),
- * 7 (32x24 warp-specialised, lid, nx % 4 == 0), 3 (32x16, periodic), 4
- * (32x16, lid), 5 (32x28, periodic), 6 (32x28, lid).  One launch per
+ * x or y, nx % 4 != 0), 2 (32x24 with loader warps, periodic, nx % 4 == 0),
+ * 7 (32x24 with loader warps, lid, nx % 4 == 0), 3 (32x16, periodic), 4
+ * (32x16, lid), 5 (32x28, periodic, nx % 4 != 0), 6 (32x28, lid,
+ * nx % 4 != 0), 8 (32x28 with loader warps, periodic, nx % 4 == 0), 9 (32x28
+ * with loader warps, lid, nx % 4 == 0).  One launch per
  * non-empty variant and step.  FP32, iterations = 2 only.  Each
  * grid's result is bit-identical to mpdata_step on that grid alone with the
  * same tile. */
@@ -278,13 +280,13 @@ int mpdata_batch_create(int ngrids, const int *dims, const int *periodic, const 
  * for the batch default (opts->tile_y); tile_y may be NULL (all default). */
 int mpdata_batch_create_tiles(int ngrids, const int *dims, const int *periodic, const int *tile_y,
                               const mpdata_opts *opts, mpdata_batch_t **out);
-/* The variant (0 .. 7, see above) that runs grid `grid`. */
+/* The variant (0 .. 9, see above) that runs grid `grid`. */
 int mpdata_batch_grid_variant(mpdata_batch_t *batch, int grid, int *variant);
 /* Device pointers (16-byte aligned) of grid `grid`; psi is advanced in
  * place.  Must be set for every grid before the first step. */
 int mpdata_batch_set_fields(mpdata_batch_t *batch, int grid, const void *h, void *psi,
                             const void *u1, const void *u2, const void *u3);
-/* Number of work items and CTAs of a variant (0 .. 7). */
+/* Number of work items and CTAs of a variant (0 .. 9). */
 int mpdata_batch_work(mpdata_batch_t *batch, int variant, int *nitems, int *ncta);
 /* Copy the current split of a variant (ncta + 1 ints) into begin. */
 int mpdata_batch_get_split(mpdata_batch_t *batch, int variant, int *begin);

@@ -205,10 +205,11 @@ class Batch:
     `grids` is a list of (nx, ny, nz) or (nx, ny, nz, (px, py, pz)); fields
     are attached per grid with set_fields."""
 
-    # 0/1: two-column 32x24 (x/y periodic / a lid; nx % 4 != 0), 2/7:
-    # warp-specialised 32x24 (periodic / lid; nx % 4 == 0), 3/4: two-column
-    # 32x16, 5/6: two-column 32x28
-    VARIANTS = 8
+    # 0/1: two-column 32x24 (x/y periodic / a lid; nx % 4 != 0), 2/7: 32x24
+    # with loader warps (periodic / lid; nx % 4 == 0), 3/4: two-column 32x16,
+    # 5/6: two-column 32x28 (nx % 4 != 0), 8/9: 32x28 with loader warps
+    # (nx % 4 == 0)
+    VARIANTS = 10
 
     def __init__(self, grids, *, nonoscillatory: bool = True, tile=(32, 24), eps: float = 1e-15,
                  periodic=(1, 1, 1), tiles=None):

@@ -12,8 +12,8 @@
 // nearly equal cost) and any other split, including the uneven ones of the
 // speed-function autotuner, can be installed instead.  A step of the batch is
 // one launch per variant; nsteps steps can be captured once into a CUDA graph
-// and replayed.  32x24 tiles of grids with nx % 4 == 0 run the
-// warp-specialised kernel, as a single-grid launch with that tile does.  Each
+// and replayed.  32x24 and 32x28 tiles of grids with nx % 4 == 0 run the
+// kernel with loader warps, as a single-grid launch with that tile does.  Each
 // tile is computed by the same code whichever CTA runs it, so every grid's
 // result is bit-identical to the single-grid launch.
 #include <stdarg.h>
@@ -37,22 +37,26 @@ namespace {
 enum Variant {
     kPairs24Periodic = 0,  // two columns per thread, tile 32x24, x and y periodic (nx % 4 != 0)
     kPairs24Lid = 1,       // same with a lid on x or y
-    kWs24Periodic = 2,     // warp-specialised tile 32x24, x and y periodic (nx % 4 == 0)
-    kPairs16Periodic = 3,  // two columns per thread, tile 32x16
+    kLd24Periodic = 2,     // tile 32x24 with loader warps, x and y periodic (nx % 4 == 0)
+    kPairs16Periodic = 3,  // two columns per thread, tile 32x16 (any nx)
     kPairs16Lid = 4,
-    kPairs28Periodic = 5,  // two columns per thread, tile 32x28
+    kPairs28Periodic = 5,  // two columns per thread, tile 32x28 (nx % 4 != 0)
     kPairs28Lid = 6,
-    kWs24Lid = 7,          // warp-specialised tile 32x24 with a lid on x or y (nx % 4 == 0)
-    kNumVariants = 8
+    kLd24Lid = 7,          // tile 32x24 with loader warps, a lid on x or y (nx % 4 == 0)
+    kLd28Periodic = 8,     // tile 32x28 with loader warps (nx % 4 == 0)
+    kLd28Lid = 9,
+    kNumVariants = 10
 };
 
 int variant_tile_y(int v) {
-    if (v == kPairs24Periodic || v == kPairs24Lid || v == kWs24Periodic || v == kWs24Lid) return 24;
-    if (v == kPairs28Periodic || v == kPairs28Lid) return 28;
+    if (v == kPairs24Periodic || v == kPairs24Lid || v == kLd24Periodic || v == kLd24Lid) return 24;
+    if (v == kPairs28Periodic || v == kPairs28Lid || v == kLd28Periodic || v == kLd28Lid) return 28;
     return 16;
 }
-bool variant_lid(int v) { return v == kPairs24Lid || v == kPairs16Lid || v == kPairs28Lid || v == kWs24Lid; }
-bool variant_ws(int v) { return v == kWs24Periodic || v == kWs24Lid; }
+bool variant_lid(int v) {
+    return v == kPairs24Lid || v == kPairs16Lid || v == kPairs28Lid || v == kLd24Lid || v == kLd28Lid;
+}
+bool variant_ld(int v) { return v == kLd24Periodic || v == kLd24Lid || v == kLd28Periodic || v == kLd28Lid; }
 
 struct Group {
     std::vector<int2> items;  // (grid, tile), by decreasing cost
@@ -194,16 +198,12 @@ int enqueue_steps(mpdata_batch *b, int nsteps, cudaStream_t s) {
             if (G.items.empty()) continue;
             const int nonosc = b->opts.nonoscillatory, lid = variant_lid(v);
             cudaError_t e;
+            const int ty = variant_tile_y(v), ld = variant_ld(v);
             if (direct[v])
-                e = variant_ws(v) ? mpdata::launch_fused_ws_direct(nonosc, lid, *direct[v], parity, s)
-                                  : mpdata::launch_fused_pairs_direct(variant_tile_y(v), nonosc, lid,
-                                                                      *direct[v], parity, s);
+                e = mpdata::launch_fused_pairs_direct(ty, ld, nonosc, lid, *direct[v], parity, s);
             else
-                e = variant_ws(v) ? mpdata::launch_fused_ws_batch(nonosc, lid, b->d_grids, G.d_items,
-                                                                  G.d_begin, G.ncta, parity, s)
-                                  : mpdata::launch_fused_pairs_batch(32, variant_tile_y(v), nonosc, lid,
-                                                                     b->d_grids, G.d_items, G.d_begin,
-                                                                     G.ncta, parity, s);
+                e = mpdata::launch_fused_pairs_batch(32, ty, ld, nonosc, lid, b->d_grids, G.d_items,
+                                                     G.d_begin, G.ncta, parity, s);
             if (e != cudaSuccess) return bcuda(e, "batched kernel launch");
         }
     }
@@ -269,10 +269,9 @@ int mpdata_batch_create_tiles(int ngrids, const int *dims, const int *periodic, 
         g.eps = (float)o.eps;
         const int ty = (tile_y && tile_y[i]) ? tile_y[i] : ty_default;
         const bool lid = !g.g.per[0] || !g.g.per[1];
-        const bool ws = ty == 24 && nx % 4 == 0;
-        const int v = ws ? (lid ? kWs24Lid : kWs24Periodic)
-                      : ty == 24 ? (lid ? kPairs24Lid : kPairs24Periodic)
-                      : ty == 28 ? (lid ? kPairs28Lid : kPairs28Periodic)
+        const bool a16 = nx % 4 == 0;
+        const int v = ty == 24 ? (a16 ? (lid ? kLd24Lid : kLd24Periodic) : (lid ? kPairs24Lid : kPairs24Periodic))
+                      : ty == 28 ? (a16 ? (lid ? kLd28Lid : kLd28Periodic) : (lid ? kPairs28Lid : kPairs28Periodic))
                                  : (lid ? kPairs16Lid : kPairs16Periodic);
         g.ntx = (nx + tx - 1) / tx;
         const int ntiles = g.ntx * ((ny + ty - 1) / ty);

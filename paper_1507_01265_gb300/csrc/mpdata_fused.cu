@@ -440,14 +440,15 @@ void fused_default_tile(int dtype, const Grid &g, int nsm, int *tx, int *ty) {
     // smallest, fastest plane; a large one the most cells per plane-time.
     struct Cand { int tx, ty; double us_aligned, us_any; };
     static const Cand cands[] = {
-        // two-column kernel; with nx % 4 == 0 (16-byte loads) the 32x24 tile
-        // runs warp-specialised.  Medians over serving-size grids with at most
-        // one tile per SM: step time / (nz + 6)
-        {32, 24, 1.76, 1.90},
-        {32, 28, 1.96, 2.47},  // 18 compute warps at 96 registers (+2 loader warps when nx % 4 == 0)
+        // two-column kernel; with nx % 4 == 0 (16-byte loads) the 32x24 and
+        // 32x28 tiles add two loader warps to their 16 / 18 compute warps.
+        // Medians over serving-size grids with at most one tile per SM: step
+        // time / (nz + 6)
+        {32, 24, 1.69, 1.90},
+        {32, 28, 1.95, 2.49},
         {32, 16, 1.40, 1.47},
         {24, 16, 1.76, 1.77},  // one-column kernel
-        {16, 16, 1.46, 1.45},
+        {16, 16, 1.45, 1.45},
     };
     const int sms = nsm > 0 ? nsm : 1 << 30;  // unknown device: every grid is one wave
     double best = 0.0;
@@ -486,12 +487,12 @@ double handout_time(long long nA, double tA, long long nB, double tB, int nsm) {
 
 bool fused_band_plan(const Grid &g, int nsm, BandPlan *plan) {
     // Rows in 28-row bands of 32x28 tiles and 24-row bands of 32x24 tiles
-    // (warp-specialised), run concurrently: SMs that finish early take the
+    // (both with loader warps), run concurrently: SMs that finish early take the
     // next tile of either height, and the 24-row bands can end near ny where
     // one tile height would leave a mostly empty band.  Per-plane times as in
     // fused_default_tile; 0.02 x the 28-row plane time covers the fork and the
     // join.
-    const double t28 = 1.96, t24 = 1.76;
+    const double t28 = 1.95, t24 = 1.69;
     if (nsm <= 0 || g.nx % 4 != 0) return false;
     const long long ntx = (g.nx + 31) / 32;
     const long long w24 = (ntx * ((g.ny + 23) / 24) + nsm - 1) / nsm, w28 = (ntx * ((g.ny + 27) / 28) + nsm - 1) / nsm;

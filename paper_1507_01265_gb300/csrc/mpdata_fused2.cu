@@ -9,13 +9,14 @@
 //   gamma  limited velocities and corrective fluxes at q2, output of q3
 //          (a5-a6), and the donor fluxes of plane p (work for the warps that
 //          the flux stage leaves idle).
-// Inputs (psi, u1, u2, u3, h) load two planes ahead into a 5-plane ring.
+// Inputs (psi, u1, u2, u3, h) load two planes ahead into a 4-plane ring.
 // Aimed at the instruction count and latency, which bound this step on GB300:
 //   * each thread owns a pair of adjacent columns (i, i+1) and evaluates both
 //     with packed f32x2 add/mul/fma, so per-thread overhead (addressing,
 //     predicates, loop control) is paid once per two cells and shared-memory
-//     neighbours of the pair come in one 64-bit load; the plane loop is
-//     unrolled by two so that register queues shift by renaming;
+//     neighbours of the pair come in one 64-bit load; the interior planes
+//     run in blocks of four so that ring slots are compile-time constants and
+//     register queues shift by renaming;
 //   * inputs stream in as 16-byte cp.async chunks when nx is a multiple of 4
 //     (chunks then never straddle a wrap or a lid and rows stay 16-byte
 //     aligned); for any other nx as 4-byte copies in element order (a warp
@@ -28,12 +29,10 @@
 //     faces are forced to zero velocity.
 // Threads are numbered from the tile outwards ring by ring in pair units, so
 // each stage's region is a prefix of the thread index.
-// The 32x24 tile of a grid with nx % 4 == 0 runs a warp-specialised form
-// (k_fused_ws): producer warps load and run the donor pass, consumer warps
-// the rest.  The 32x28 tile of such a grid adds two loader warps to its 18
-// (pairs_loader): they issue and wait for every input load, so the compute
-// threads hold no load state (fewer spills) and no load instructions, and the
-// 20 warps spread 5 to each scheduler.
+// The 32x24 and 32x28 tiles of a grid with nx % 4 == 0 add two loader warps
+// to their 16 / 18 compute warps (pairs_loader): they issue and wait for
+// every input load, so the compute threads hold no load state (fewer spills)
+// and no load instructions.
 #include <type_traits>
 
 #include "mpdata_internal.cuh"
@@ -123,6 +122,7 @@ struct Lay2 {
     static constexpr int PL = EX * EY;
     static constexpr int PLL = EXL * EY;        // loaded elements per plane
     static constexpr int NT = NPX * (TY + 4);   // psi1 region = threads
+    static constexpr int NTW = (NT + 31) / 32 * 32;  // NT in whole warps
     static constexpr int N_OUT = HX * TY;
     static constexpr int N_VM = (HX + 1) * (TY + 1);
     static constexpr int N_BETA = NPX * (TY + 2);
@@ -148,6 +148,7 @@ __device__ __forceinline__ void onion2(int t, int &px, int &ry) {
     using L = Lay2<TX, TY>;
     constexpr int HX = L::HX;
     if (t < L::N_OUT) { px = 2 + t % HX; ry = t / HX; return; }
+    if (t >= L::NT) { px = HX + 4; ry = t - L::NT; return; }  // idle: row padding
     t -= L::N_OUT;
     if (t < HX) { px = 2 + t; ry = TY; return; }
     t -= HX;
@@ -221,9 +222,9 @@ using IC = std::integral_constant<int, V>;
 using BT = std::integral_constant<bool, true>;
 using BF = std::integral_constant<bool, false>;
 
-// Loader warps of the two-column tile (k_fused_pairs with LD): threads NT ..
-// NT + 63 issue every 16-byte input load of the tile and wait for them, on the
-// same schedule and with the same barriers (three per plane and one at the
+// Loader warps of the two-column tile (k_fused_pairs with LD): threads NTW ..
+// NTW + 63 issue every 16-byte input load of the tile and wait for them, on
+// the same schedule and with the same barriers (three per plane and one at the
 // end) as pairs_tile, so that the compute threads carry no load state.
 template <int TX, int TY, bool LID>
 __device__ __forceinline__ void pairs_loader(const TileArgs &a, int tile, float *sm) {
@@ -239,7 +240,7 @@ __device__ __forceinline__ void pairs_loader(const TileArgs &a, int tile, float 
     const int ntx = a.ntx;
     const int x0 = (tile % ntx) * TX, y0 = a.y0 + (tile / ntx) * TY;
     const unsigned sm_base = (unsigned)__cvta_generic_to_shared(sm);
-    const int j = threadIdx.x - L::NT;
+    const int j = threadIdx.x - L::NTW;
     int ld_off[KCH];
     unsigned ld_dst[KCH];
     unsigned cfl = 0;  // per chunk k: bit k has, 8+k lid ghost, 16+k y-lid face, 24+k x-lid face
@@ -309,8 +310,13 @@ __device__ __forceinline__ void pairs_tile(const TileArgs &a, int tile, float *s
     using L = Lay2<TX, TY, 4>;
     static_assert(!LD || AL == 1, "loader warps take the 16-byte loads only");
     // __syncthreads is an aligned barrier: every warp must reach each one at
-    // one code location, so the loader threads must form whole warps
-    static_assert(!LD || L::NT % 32 == 0, "loader threads must be whole warps");
+    // one code location, so the loader threads form whole warps and the
+    // threads NT .. NTW - 1 that fill the last compute warp run the compute
+    // path idle, placed by onion2 on the row padding (idle thread k stores to
+    // words 2HX + 8, 2HX + 9 of row k + 3 of a plane and reads one word and
+    // one row around them; no stage touches those words)
+    static_assert(!LD || L::NTW - L::NT <= L::EY - 4, "idle threads: one padding row each");
+    static_assert(!LD || 2 * (L::HX + 4) + 3 <= L::EX, "idle threads stay inside the row pitch");
     const Grid &g = a.g;
     const float eps1 = a.eps;
     const float *__restrict__ h = a.h;
@@ -337,7 +343,7 @@ __device__ __forceinline__ void pairs_tile(const TileArgs &a, int tile, float *s
     const F2 eps = bc(eps1);
 
     if constexpr (LD) {
-        if (t >= L::NT) {
+        if (t >= L::NTW) {
             pairs_loader<TX, TY, LID>(a, tile, sm);
             return;
         }
@@ -660,421 +666,8 @@ __device__ __forceinline__ void pairs_tile(const TileArgs &a, int tile, float *s
     __syncthreads();
 }
 
-// ---------------------------------------------------------------------------
-// Warp-specialised form of the 32x24 tile (nx % 4 == 0; any boundaries).
-// Warps 0-15 (consumers) run stages a2-a6 of plane q2 and the output of q3,
-// with two consumer-only barriers per plane; warps 16-19 (producers) issue
-// every input load and run the donor pass (a1) of plane p for the whole psi1
-// region, four column pairs per thread.  psi1 planes rotate through three
-// shared slots (producers write p while consumers read p-1 and p-2), and one
-// CTA barrier per plane hands them over.  setmaxnreg moves registers from the
-// producers (64) to the consumers (104); the block's total is unchanged
-// (20 x 32 x 96 = 16 x 32 x 104 + 4 x 32 x 64) and every SM sub-partition
-// holds 4 x 32 x 104 + 32 x 64 of its 16 K.  Same arithmetic, operation for
-// operation, as pairs_tile, so the result is bit-identical.  ws_tile with
-// ROLE 2 runs one tile with both roles and moves the registers itself, after
-// the set-up both share; ROLE 0 (producers, threads 512..639) or 1
-// (consumers, 0..511) runs one role of one tile, for a kernel that moves the
-// registers once and loops over tiles (the roles run the same number of
-// planes, so their CTA barriers pair up, and no shared memory is read after a
-// tile's last one).
-__device__ __forceinline__ void named_sync(int id, int count) {
-    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
-}
-
-template <bool NONOSC, bool LID, int ROLE>
-__device__ __forceinline__ void ws_tile(const TileArgs &a, int tile, float *sm) {
-    constexpr int TX = 32, TY = 24;
-    using L = Lay2<TX, TY>;
-    const Grid &g = a.g;
-    const float eps1 = a.eps;
-    const float *__restrict__ h = a.h;
-    const float *__restrict__ psi = a.psi;
-    const float *__restrict__ u1 = a.u1;
-    const float *__restrict__ u2 = a.u2;
-    const float *__restrict__ u3 = a.u3;
-    float *__restrict__ out = a.out;
-    const int ntx = a.ntx;
-    constexpr int EX = L::EX, PL = L::PL;
-    constexpr int PB = PL * 4;
-    constexpr int FB = L::NR * PB;
-    constexpr int RB = EX * 4;
-    // planes: ring 0..24, psi1 25..27 (three slots), SX 28-29, SY 30-31, SZ 32,
-    // V1 33, V2 34, BU 35, BD 36, GX 37, GY 38
-    constexpr int oP1 = 25 * PB, oSX = 28 * PB, oSY = 30 * PB, oSZ = 32 * PB;
-    constexpr int oV1 = 33 * PB, oV2 = 34 * PB, oBU = 35 * PB, oBD = 36 * PB;
-    constexpr int oGX = 37 * PB, oGY = 38 * PB;
-    constexpr int NC = 512;  // consumer threads
-    const unsigned sm_base = (unsigned)__cvta_generic_to_shared(sm);
-
-    const int t = threadIdx.x;
-    const int nx = g.nx, ny = g.ny, nz = g.nz;
-    const int perx = LID ? g.per[0] : 1, pery = LID ? g.per[1] : 1, perz = g.per[2];
-    const long long nxy = (long long)nx * ny;
-    const int x0 = (tile % ntx) * TX, y0 = a.y0 + (tile / ntx) * TY;
-    const F2 eps = bc(eps1);
-    const int p_first = perz ? -3 : -1;
-    const int p_last = nz + 2;
-    const int q1lo = perz ? -2 : 0, q1hi = perz ? nz + 1 : nz - 1;
-    const int q1top = perz ? q1hi : nz;
-    const int wlo = perz ? -2 : 0, whi = perz ? nz : nz - 2;
-    const int vlo = perz ? -1 : 0, vhi = perz ? nz : nz - 1;
-    auto slot3 = [](int q) {
-        const int r = q % 3;
-        return r < 0 ? r + 3 : r;
-    };
-
-    if (ROLE == 0 || (ROLE == 2 && t >= NC)) {
-        // ================= producers =================
-        if constexpr (ROLE == 2) asm volatile("setmaxnreg.dec.sync.aligned.u32 64;\n" ::: "memory");
-        const int j = t - NC;
-        int ld_off[3];
-        unsigned ld_dst[3];
-        // per chunk c: bit c has, bit c + 4 lid ghost (zero), c + 8 y-lid face 0 (u2 zero),
-        // c + 12 x-lid face 0 (u1 patched after the copy)
-        unsigned cf = 0;
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            const int idx = j + 128 * c;
-            ld_off[c] = 0;
-            ld_dst[c] = 0;
-            if (idx < L::NCH) {
-                const int ey = idx / L::CPR, cc = idx % L::CPR;
-                const int lx = x0 - 4 + 4 * cc, ly = y0 - 3 + ey;
-                if constexpr (LID) {
-                    int cx, cy;
-                    bool outx = false, outy = false;
-                    if (perx) cx = wrap(lx, nx); else { outx = lx < 0 || lx >= nx; cx = outx ? 0 : lx; }
-                    if (pery) cy = wrap(ly, ny); else { outy = ly < 0 || ly >= ny; cy = outy ? 0 : ly; }
-                    ld_off[c] = cy * nx + cx;
-                    cf |= (unsigned)(outx || outy) << (c + 4);
-                    cf |= (unsigned)(outx || outy || (!pery && ly == 0)) << (c + 8);
-                    cf |= (unsigned)(!perx && lx == 0) << (c + 12);
-                } else {
-                    ld_off[c] = wrap(ly, ny) * nx + wrap(lx, nx);
-                }
-                ld_dst[c] = sm_base + (unsigned)(ey * EX + 4 * cc) * 4u;
-                cf |= 1u << c;
-            }
-        }
-        auto issue = [&](int p) {
-            const long long pz = (long long)(perz ? wrap(p, nz) : min(max(p, 0), nz - 1)) * nxy;
-            const bool zz = !perz && (p <= 0 || p >= nz);  // z-lid face
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                if ((cf >> c) & 1u) {
-                    const long long pc = pz + ld_off[c];
-                    const unsigned d = ld_dst[c] + (unsigned)(slot5(p) * PB);
-                    if constexpr (LID) {
-                        const bool zall = (cf >> (c + 4)) & 1u;
-                        cp16(d, psi + pc, zall);
-                        cp16(d + FB, u1 + pc, zall);
-                        cp16(d + 2 * FB, u2 + pc, (cf >> (c + 8)) & 1u);
-                        cp16(d + 3 * FB, u3 + pc, zall || zz);
-                        cp16(d + 4 * FB, h + pc, zall);
-                    } else {
-                        cp16(d, psi + pc, false);
-                        cp16(d + FB, u1 + pc, false);
-                        cp16(d + 2 * FB, u2 + pc, false);
-                        cp16(d + 3 * FB, u3 + pc, zz);
-                        cp16(d + 4 * FB, h + pc, false);
-                    }
-                }
-            }
-            asm volatile("cp.async.commit_group;\n" ::: "memory");
-        };
-        unsigned tbk[4];
-        // per pair i: bit i valid, i + 4 clamp left, i + 8 clamp right, i + 12 clamp
-        // below, i + 16 clamp above (zero-gradient ghosts behind a lid)
-        unsigned hk = 0;
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const int k = j + 128 * i;
-            int px = 1, ry = -2;
-            if (k < L::NT) {
-                onion2<TX, TY>(k, px, ry);
-                hk |= 1u << i;
-                if constexpr (LID) {
-                    const int gxk = x0 + 2 * px - 4, gyk = y0 + ry;
-                    hk |= (unsigned)(!perx && gxk == 0) << (i + 4);
-                    hk |= (unsigned)(!perx && gxk + 1 == nx - 1) << (i + 8);
-                    hk |= (unsigned)(!pery && gyk == 0) << (i + 12);
-                    hk |= (unsigned)(!pery && gyk == ny - 1) << (i + 16);
-                }
-            }
-            tbk[i] = sm_base + (unsigned)((ry + 3) * EX + 2 * px) * 4u;
-        }
-        issue(p_first);
-        issue(p_first + 1);
-        for (int p = p_first; p <= p_last; ++p) {
-            if (p + 2 <= p_last) issue(p + 2);
-            else asm volatile("cp.async.commit_group;\n" ::: "memory");
-            asm volatile("cp.async.wait_group 1;\n" ::: "memory");  // plane p+1 landed
-            if (LID) {
-#pragma unroll
-                for (int c = 0; c < 3; ++c)
-                    if ((cf >> (c + 12)) & 1u)
-                        sm[(ld_dst[c] - sm_base) / 4u + (unsigned)(L::NR * PL + slot5(p + 1) * PL)] = 0.f;
-            }
-            named_sync(2, 128);
-            if (p >= q1lo && p <= q1top) {
-                const unsigned so = (unsigned)(slot3(p) * PB + oP1);
-                const unsigned sprev = (unsigned)(slot3(p - 1) * PB + oP1);
-                const unsigned rm = (unsigned)(slot5(p - 1) * PB), rq = (unsigned)(slot5(p) * PB),
-                               rn = (unsigned)(slot5(p + 1) * PB);
-#pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    if (!((hk >> i) & 1u)) continue;
-                    const unsigned b = tbk[i];
-                    F2 p1n;
-                    if (p <= q1hi) {
-                        const unsigned rp = b + rq;
-                        const F2 pn_p = ldp<0>(rp), pn_c = ldp<0>(b + rm), pn_n = ldp<0>(b + rn);
-                        const F2 u1p = ldp<FB>(rp), u2p = ldp<2 * FB>(rp), u3p = ldp<3 * FB>(rp), hp = ldp<4 * FB>(rp);
-                        const F2 u3n = ldp<3 * FB>(b + rn);
-                        F2 fxl, fxh, fyl, fyh;
-                        if constexpr (LID) {  // a clamped neighbour is the cell itself
-                            const float xl = lds<-4>(rp), xr = lds<8>(rp);
-                            F2 yd = ldp<-RB>(rp), yu = ldp<RB>(rp);
-                            F2 lsh = make_float2(xl, pn_p.x), rsh = make_float2(pn_p.y, xr);
-                            if ((hk >> (i + 4)) & 1u) lsh.x = pn_p.x;
-                            if ((hk >> (i + 8)) & 1u) rsh.y = pn_p.y;
-                            if ((hk >> (i + 12)) & 1u) yd = pn_p;
-                            if ((hk >> (i + 16)) & 1u) yu = pn_p;
-                            fxl = flux(u1p, lsh, pn_p);
-                            fxh = flux(make_float2(u1p.y, lds<FB + 8>(rp)), pn_p, rsh);
-                            fyl = flux(u2p, yd, pn_p);
-                            fyh = flux(ldp<2 * FB + RB>(rp), pn_p, yu);
-                        } else {
-                            fxl = flux(u1p, make_float2(lds<-4>(rp), pn_p.x), pn_p);
-                            fxh = flux(make_float2(u1p.y, lds<FB + 8>(rp)), pn_p, make_float2(pn_p.y, lds<8>(rp)));
-                            fyl = flux(u2p, ldp<-RB>(rp), pn_p);
-                            fyh = flux(ldp<2 * FB + RB>(rp), pn_p, ldp<RB>(rp));
-                        }
-                        const F2 fzl = flux(u3p, pn_c, pn_p);
-                        const F2 fzh = flux(u3n, pn_p, pn_n);
-                        const F2 div = add(add(sub(fxh, fxl), sub(fyh, fyl)), sub(fzh, fzl));
-                        p1n = sub(pn_p, mul(div, rcp(hp)));
-                    } else {  // lid top ghost: zero-gradient copy of the plane below
-                        p1n = ldp<0>(b + sprev);
-                    }
-                    stp<0>(b + so, p1n);
-                }
-            }
-            __syncthreads();  // (X)
-        }
-        asm volatile("cp.async.wait_all;\n" ::: "memory");
-        return;
-    }
-
-    // ================= consumers =================
-    if constexpr (ROLE == 2) asm volatile("setmaxnreg.inc.sync.aligned.u32 104;\n" ::: "memory");
-    const bool in_t = t < L::NT;
-    int px = 1, ry = -2;
-    if (in_t) onion2<TX, TY>(t, px, ry);
-    const int gx = x0 + 2 * px - 4, gy = y0 + ry;
-    const unsigned tb = sm_base + (unsigned)((ry + 3) * EX + 2 * px) * 4u;
-    const bool in_vm = t < L::N_VM, in_beta = t < L::N_BETA, in_v = t < L::N_V, in_out = t < L::N_OUT;
-    const bool store = in_out && gx < nx && gy < ny;
-    float *const outp = out + (long long)gy * nx + gx;
-    // lid handling (LID only), as in pairs_tile: clamped cell neighbours,
-    // zero-velocity lid faces
-    const bool clampL = LID && !perx && gx == 0;
-    const bool clampR = LID && !perx && gx + 1 == nx - 1;
-    const int dD = (LID && !pery && gy == 0) ? 0 : -RB;
-    const int dU = (LID && !pery && gy == ny - 1) ? 0 : RB;
-    const bool xlid0 = LID && !perx && (gx <= 0 || gx >= nx);
-    const bool xlid1 = LID && !perx && (gx + 1 <= 0 || gx + 1 >= nx);
-    const bool ylid = LID && !pery && (gy <= 0 || gy >= ny);
-    auto ldD = [&](unsigned b) { if constexpr (LID) return ldp<0>(b + dD); else return ldp<-RB>(b); };
-    auto ldU = [&](unsigned b) { if constexpr (LID) return ldp<0>(b + dU); else return ldp<RB>(b); };
-    auto lshC = [&](unsigned b, F2 own) { const float x = lds<-4>(b); return make_float2(clampL ? own.x : x, own.x); };
-    auto rshC = [&](unsigned b, F2 own) { const float x = lds<8>(b); return make_float2(own.y, clampR ? own.y : x); };
-    auto lshF = [&](unsigned b, F2 own) { return make_float2(lds<-4>(b), own.x); };
-    auto rshF = [&](unsigned b, F2 own) { return make_float2(own.y, lds<8>(b)); };
-    auto lid2 = [&](F2 v, bool a0, bool c0) { return make_float2(a0 ? 0.f : v.x, c0 ? 0.f : v.y); };
-
-    const F2 Z = bc(0.f);
-    F2 pn_mm = Z, pn_m = Z, pn_c = Z;
-    F2 p1a = Z, p1b = Z, p1c = Z;
-    F2 u1b = Z, u2b = Z, u3b = Z, hb = bc(1.f);
-    F2 u1c = Z, u2c = Z, u3c = Z, hc = bc(1.f);
-    F2 sxa = Z, sxb = Z, sya = Z, syb = Z;
-    F2 wlo_v = Z, bu_prev = Z, bd_prev = Z, h_prev = bc(1.f);
-    F2 dacc = Z, gx_own = Z, gy_own = Z;
-
-#pragma unroll 2
-    for (int p = p_first; p <= p_last; ++p) {
-        const int q1 = p - 1, q2 = p - 2, q3 = p - 3;
-        const unsigned r2 = tb + (unsigned)(slot5(q2) * PB);
-        const unsigned r1 = tb + (unsigned)(slot5(q1) * PB);
-        const unsigned b1 = tb + (unsigned)((q1 & 1) * PB);  // SX/SY slot of q1
-        const unsigned b2 = tb + (unsigned)((q2 & 1) * PB);  // SX/SY slot of q2
-        const unsigned c1 = tb + (unsigned)(slot3(q1) * PB) + oP1;  // psi1 of q1
-        const unsigned c2 = tb + (unsigned)(slot3(q2) * PB) + oP1;  // psi1 of q2
-        // own inputs and psi1 of plane q1 (loaded two iterations ago, donor of the last one)
-        pn_c = ldp<0>(r1);
-        u1c = ldp<FB>(r1);
-        u2c = ldp<2 * FB>(r1);
-        u3c = ldp<3 * FB>(r1);
-        hc = ldp<4 * FB>(r1);
-        if (q1 >= q1lo && q1 <= q1top) p1c = ldp<0>(c1);
-
-        // ---- alpha ----
-        if (in_out && q3 >= 0 && q3 <= nz - 1) {
-            const F2 gxr = rshF(tb + oGX, gx_own), gyu = ldp<oGY + RB>(tb);
-            dacc = add(add(sub(gxr, gx_own), sub(gyu, gy_own)), dacc);
-        }
-        F2 sxc = sxb, syc = syb, v1_own = Z, v2_own = Z, pl = Z, pd = Z;
-        if (in_t && q1 >= q1lo && q1 <= q1top) {
-            sxc = add(lshC(c1, p1c), p1c);
-            syc = add(ldp<-RB>(c1), p1c);
-            stp<oSX>(b1, sxc);
-            stp<oSY>(b1, syc);
-            stp<oSZ>(tb, add(p1b, p1c));
-        }
-        if (!perz && q1 == 0) { p1b = p1c; sxb = sxc; syb = syc; }
-        if (in_v && q2 >= vlo && q2 <= vhi) {
-            pl = lshF(c2, p1b);
-            pd = ldp<-RB>(c2);
-            {   // x-faces
-                const F2 u2U = ldp<2 * FB + RB>(r2);
-                const F2 ua = add(add(add(lshF(r2 + 2 * FB, u2b), u2b),
-                                      make_float2(lds<2 * FB + RB - 4>(r2), u2U.x)), u2U);
-                const F2 ub = add(add(add(lshF(r2 + 3 * FB, u3b), u3b), lshF(r1 + 3 * FB, u3c)), u3c);
-                const F2 v = pseudo_velocity(u1b, p1b, pl, sxb, ldU(b2 + oSX), ldD(b2 + oSX), ua, sxc, sxa,
-                                             ub, add(lshF(r2 + 4 * FB, hb), hb), eps);
-                v1_own = LID ? lid2(v, xlid0, xlid1) : v;
-            }
-            {   // y-faces
-                const F2 u1D = ldp<FB - RB>(r2);
-                const F2 va = add(add(add(ldp<3 * FB - RB>(r2), u3b), ldp<3 * FB - RB>(r1)), u3c);
-                const F2 vb = add(add(add(u1D, u1b), make_float2(u1D.y, lds<FB - RB + 8>(r2))),
-                                  rshF(r2 + FB, u1b));
-                const F2 v = pseudo_velocity(u2b, p1b, pd, syb, syc, sya, va, rshC(b2 + oSY, syb),
-                                             lshC(b2 + oSY, syb), vb, add(ldp<4 * FB - RB>(r2), hb), eps);
-                v2_own = (LID && ylid) ? Z : v;
-            }
-            stp<oV1>(tb, v1_own);
-            stp<oV2>(tb, v2_own);
-        }
-        named_sync(1, NC);  // (F)
-
-        // ---- beta ----
-        F2 whi_v = Z, bu_c = Z, bd_c = Z;
-        if (in_beta) {
-            if (q2 >= wlo && q2 <= whi) {
-                const F2 szo = add(p1b, p1c);
-                const F2 ua = add(add(add(u1b, u1c), rshF(r2 + FB, u1b)), rshF(r1 + FB, u1c));
-                const F2 ub = add(add(add(u2b, u2c), ldp<2 * FB + RB>(r2)), ldp<2 * FB + RB>(r1));
-                F2 szu, szd;
-                if constexpr (LID) {
-                    szu = ldU(tb + oSZ);
-                    szd = ldD(tb + oSZ);
-                } else {
-                    szu = ldp<oSZ + RB>(tb);
-                    szd = ldp<oSZ - RB>(tb);
-                }
-                whi_v = pseudo_velocity(u3c, p1c, p1b, szo, rshC(tb + oSZ, szo), lshC(tb + oSZ, szo), ua,
-                                        szu, szd, ub, add(hb, hc), eps);
-            }
-            if (NONOSC && q2 >= vlo && q2 <= vhi) {
-                const F2 aL = lshC(r2, pn_m), aR = rshC(r2, pn_m), aD = ldD(r2), aU = ldU(r2);
-                const F2 bL = lshC(c2, p1b), bR = rshC(c2, p1b);
-                const F2 bD = ldD(c2), bU = ldU(c2);
-                F2 mx = max3(max3(aL, aR, aD), max3(aU, bL, bR), max3(bD, bU, pn_mm));
-                mx = max3(mx, max3(pn_m, pn_c, p1a), max3(p1b, p1c, p1b));
-                F2 mn = min3(min3(aL, aR, aD), min3(aU, bL, bR), min3(bD, bU, pn_mm));
-                mn = min3(mn, min3(pn_m, pn_c, p1a), min3(p1b, p1c, p1b));
-                const F2 v1h = rshF(tb + oV1, v1_own), v2h = ldp<oV2 + RB>(tb);
-                const F2 in = add(add(sub(mul(pos(v1_own), bL), mul(neg(v1h), bR)),
-                                      sub(mul(pos(v2_own), bD), mul(neg(v2h), bU))),
-                                  sub(mul(pos(wlo_v), p1a), mul(neg(whi_v), p1c)));
-                const F2 outf = mul(add(add(sub(pos(v1h), neg(v1_own)), sub(pos(v2h), neg(v2_own))),
-                                        sub(pos(whi_v), neg(wlo_v))), p1b);
-                bu_c = mul(mul(sub(mx, p1b), hb), rcp(add(in, eps)));
-                bd_c = mul(mul(sub(p1b, mn), hb), rcp(add(outf, eps)));
-                stp<oBU>(tb, bu_c);
-                stp<oBD>(tb, bd_c);
-            }
-        }
-        named_sync(1, NC);  // (H)
-
-        // ---- gamma ----
-        if (in_vm && q2 >= 0 && q2 <= nz - 1) {
-            F2 vm1 = v1_own, vm2 = v2_own;
-            if (NONOSC) {
-                const F2 buL = lshF(tb + oBU, bu_c), bdL = lshF(tb + oBD, bd_c);
-                const F2 buD = ldp<oBU - RB>(tb), bdD = ldp<oBD - RB>(tb);
-                const F2 one = bc(1.f);
-                vm1 = add(mul(pos(v1_own), min3(one, bdL, bu_c)), mul(neg(v1_own), min3(one, buL, bd_c)));
-                vm2 = add(mul(pos(v2_own), min3(one, bdD, bu_c)), mul(neg(v2_own), min3(one, buD, bd_c)));
-            }
-            gx_own = flux(vm1, pl, p1b);
-            gy_own = flux(vm2, pd, p1b);
-            if (LID) {
-                gx_own = lid2(gx_own, xlid0, xlid1);
-                gy_own = ylid ? Z : gy_own;
-            }
-            stp<oGX>(tb, gx_own);
-            stp<oGY>(tb, gy_own);
-        }
-        const bool q3ok = q3 >= 0 && q3 <= nz - 1, q2ok = q2 >= 0 && q2 <= nz - 1;
-        if (in_out && (q3ok || q2ok)) {
-            F2 gz = Z;
-            if (perz || (q2 >= 1 && q2 <= nz - 1)) {
-                F2 vm3 = wlo_v;
-                if (NONOSC) {
-                    const F2 one = bc(1.f);
-                    vm3 = add(mul(pos(wlo_v), min3(one, bd_prev, bu_c)), mul(neg(wlo_v), min3(one, bu_prev, bd_c)));
-                }
-                gz = flux(vm3, p1a, p1b);
-            }
-            if (q3ok && store) st2(outp + (long long)q3 * nxy, sub(p1a, mul(add(dacc, gz), rcp(h_prev))));
-            dacc = sub(Z, gz);
-        }
-        __syncthreads();  // (X)
-
-        h_prev = hb;
-        pn_mm = pn_m; pn_m = pn_c;
-        u1b = u1c; u2b = u2c; u3b = u3c; hb = hc;
-        p1a = p1b; p1b = p1c;
-        sxa = sxb; sxb = sxc; sya = syb; syb = syc;
-        wlo_v = whi_v; bu_prev = bu_c; bd_prev = bd_c;
-    }
-}
-
-template <bool NONOSC, bool LID>
-__global__ void __launch_bounds__(640, 1) k_fused_ws(TileArgs a) {
-    extern __shared__ __align__(16) float sm[];
-    ws_tile<NONOSC, LID, 2>(a, blockIdx.x, sm);
-}
-
-// Batched form: CTA c runs the 32x24 tiles [begin[c], begin[c+1]) of the item
-// list (grids with nx % 4 == 0), each role looping over them.
-template <bool NONOSC, bool LID>
-__global__ void __launch_bounds__(640, 1)
-    k_fused_ws_batch(const BatchGrid *__restrict__ grids, const int2 *__restrict__ items,
-                     const int *__restrict__ begin, int parity) {
-    extern __shared__ __align__(16) float sm[];
-    const int lo = begin[blockIdx.x], hi = begin[blockIdx.x + 1];
-    if (threadIdx.x >= 512) {
-        asm volatile("setmaxnreg.dec.sync.aligned.u32 64;\n" ::: "memory");
-        for (int it = lo; it < hi; ++it) {
-            const int2 w = items[it];
-            ws_tile<NONOSC, LID, 0>(batch_args(grids[w.x], parity), w.y, sm);
-        }
-    } else {
-        asm volatile("setmaxnreg.inc.sync.aligned.u32 104;\n" ::: "memory");
-        for (int it = lo; it < hi; ++it) {
-            const int2 w = items[it];
-            ws_tile<NONOSC, LID, 1>(batch_args(grids[w.x], parity), w.y, sm);
-        }
-    }
-}
-
 template <int TX, int TY, bool NONOSC, bool LID, int AL, bool LD = false>
-__global__ void __launch_bounds__(Lay2<TX, TY>::NT + (LD ? 64 : 0), 1) k_fused_pairs(TileArgs a) {
+__global__ void __launch_bounds__(LD ? Lay2<TX, TY>::NTW + 64 : Lay2<TX, TY>::NT, 1) k_fused_pairs(TileArgs a) {
     extern __shared__ __align__(16) float sm[];
     pairs_tile<TX, TY, NONOSC, LID, AL, LD>(a, blockIdx.x, sm);
 }
@@ -1082,15 +675,15 @@ __global__ void __launch_bounds__(Lay2<TX, TY>::NT + (LD ? 64 : 0), 1) k_fused_p
 // Persistent batched launch: CTA c runs work items [begin[c], begin[c+1]) of
 // the item list, each item a (grid, tile) pair; parity selects which buffer
 // of each grid's (psi, scratch) pair is read.
-template <int TX, int TY, bool NONOSC, bool LID>
-__global__ void __launch_bounds__(Lay2<TX, TY>::NT, 1)
+template <int TX, int TY, bool NONOSC, bool LID, bool LD = false>
+__global__ void __launch_bounds__(LD ? Lay2<TX, TY>::NTW + 64 : Lay2<TX, TY>::NT, 1)
     k_fused_pairs_batch(const BatchGrid *__restrict__ grids, const int2 *__restrict__ items,
                         const int *__restrict__ begin, int parity) {
     extern __shared__ __align__(16) float sm[];
     const int lo = begin[blockIdx.x], hi = begin[blockIdx.x + 1];
     for (int it = lo; it < hi; ++it) {
         const int2 w = items[it];
-        pairs_tile<TX, TY, NONOSC, LID, 2>(batch_args(grids[w.x], parity), w.y, sm);
+        pairs_tile<TX, TY, NONOSC, LID, LD ? 1 : 2, LD>(batch_args(grids[w.x], parity), w.y, sm);
     }
 }
 
@@ -1106,78 +699,96 @@ __device__ __forceinline__ int direct_run(const DirectBatch &d, int c) {
     return lo;
 }
 
-template <int TX, int TY, bool NONOSC, bool LID>
-__global__ void __launch_bounds__(Lay2<TX, TY>::NT, 1)
+template <int TX, int TY, bool NONOSC, bool LID, bool LD = false>
+__global__ void __launch_bounds__(LD ? Lay2<TX, TY>::NTW + 64 : Lay2<TX, TY>::NT, 1)
     k_fused_pairs_direct(const __grid_constant__ DirectBatch d, int parity) {
     extern __shared__ __align__(16) float sm[];
     const int c = blockIdx.x, r = direct_run(d, c);
-    pairs_tile<TX, TY, NONOSC, LID, 2>(batch_args(d.g[r], parity), d.tile0[r] + c - d.start[r], sm);
+    pairs_tile<TX, TY, NONOSC, LID, LD ? 1 : 2, LD>(batch_args(d.g[r], parity), d.tile0[r] + c - d.start[r], sm);
 }
 
-template <bool NONOSC, bool LID>
-__global__ void __launch_bounds__(640, 1) k_fused_ws_direct(const __grid_constant__ DirectBatch d, int parity) {
-    extern __shared__ __align__(16) float sm[];
-    const int c = blockIdx.x, r = direct_run(d, c);
-    ws_tile<NONOSC, LID, 2>(batch_args(d.g[r], parity), d.tile0[r] + c - d.start[r], sm);
+// Loader warps serve the 24- and 28-row tiles of launches whose grids all have
+// nx % 4 == 0 (16-byte loads); 16-row tiles and any other nx keep the
+// compute threads' own loads.
+template <int TY>
+constexpr bool has_loaders() { return TY == 24 || TY == 28; }
+
+template <int TX, int TY>
+constexpr int pairs_threads(bool ld) { return ld ? Lay2<TX, TY>::NTW + 64 : Lay2<TX, TY>::NT; }
+
+template <int TX, int TY>
+constexpr size_t pairs_smem() {  // the two-column kernel's 4-plane ring
+    return (size_t)Lay2<TX, TY, 4>::NPLANES * Lay2<TX, TY, 4>::PL * sizeof(float);
+}
+
+using SingleKernel = void (*)(TileArgs);
+
+template <int TX, int TY, int AL, bool LD>
+SingleKernel single_kernel(int nonosc, bool lid) {
+    return nonosc ? (lid ? k_fused_pairs<TX, TY, true, true, AL, LD> : k_fused_pairs<TX, TY, true, false, AL, LD>)
+                  : (lid ? k_fused_pairs<TX, TY, false, true, AL, LD> : k_fused_pairs<TX, TY, false, false, AL, LD>);
+}
+
+template <int TX, int TY>
+SingleKernel pick_single(const Grid &g, int nonosc, bool &ld) {
+    const bool lid = !g.per[0] || !g.per[1];
+    const bool a16 = g.nx % 4 == 0;
+    ld = false;
+    if (!a16) return single_kernel<TX, TY, 0, false>(nonosc, lid);
+    if constexpr (has_loaders<TY>()) {
+        ld = true;
+        return single_kernel<TX, TY, 1, true>(nonosc, lid);
+    } else {
+        return single_kernel<TX, TY, 1, false>(nonosc, lid);
+    }
+}
+
+TileArgs tile_args(const Grid &g, double eps, int tx, int y0, const void *h, const void *psi,
+                   const void *u1, const void *u2, const void *u3, void *out) {
+    TileArgs a;
+    a.g = g;
+    a.ntx = (g.nx + tx - 1) / tx;
+    a.y0 = y0;
+    a.eps = (float)eps;
+    a.h = (const float *)h; a.psi = (const float *)psi; a.u1 = (const float *)u1;
+    a.u2 = (const float *)u2; a.u3 = (const float *)u3; a.out = (float *)out;
+    return a;
 }
 
 template <int TX, int TY>
 cudaError_t launch_pairs(const Grid &g, int nonosc, double eps, const void *h, const void *psi,
                          const void *u1, const void *u2, const void *u3, void *out, cudaStream_t s) {
-    using L = Lay2<TX, TY, 4>;  // the two-column kernel's 4-plane ring
-    const size_t smem = (size_t)L::NPLANES * L::PL * sizeof(float);
-    const int ntx = (g.nx + TX - 1) / TX, nty = (g.ny + TY - 1) / TY;
-    const bool lid = !g.per[0] || !g.per[1];
-    const bool a16 = g.nx % 4 == 0;
-    void (*kern)(TileArgs);
-    if (a16)
-        kern = nonosc ? (lid ? k_fused_pairs<TX, TY, true, true, 1> : k_fused_pairs<TX, TY, true, false, 1>)
-                      : (lid ? k_fused_pairs<TX, TY, false, true, 1> : k_fused_pairs<TX, TY, false, false, 1>);
-    else
-        kern = nonosc ? (lid ? k_fused_pairs<TX, TY, true, true, 0> : k_fused_pairs<TX, TY, true, false, 0>)
-                      : (lid ? k_fused_pairs<TX, TY, false, true, 0> : k_fused_pairs<TX, TY, false, false, 0>);
-    int nthreads = L::NT;
-    if constexpr (TY == 28) {  // two loader warps issue the 16-byte loads (NT is 18 whole warps)
-        if (a16) {
-            kern = nonosc ? (lid ? k_fused_pairs<TX, TY, true, true, 1, true> : k_fused_pairs<TX, TY, true, false, 1, true>)
-                          : (lid ? k_fused_pairs<TX, TY, false, true, 1, true> : k_fused_pairs<TX, TY, false, false, 1, true>);
-            nthreads = L::NT + 64;
-        }
-    }
+    const size_t smem = pairs_smem<TX, TY>();
+    bool ld;
+    const SingleKernel kern = pick_single<TX, TY>(g, nonosc, ld);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    TileArgs a;
-    a.g = g;
-    a.ntx = ntx;
-    a.y0 = 0;
-    a.eps = (float)eps;
-    a.h = (const float *)h; a.psi = (const float *)psi; a.u1 = (const float *)u1;
-    a.u2 = (const float *)u2; a.u3 = (const float *)u3; a.out = (float *)out;
-    if constexpr (TX == 32 && TY == 24) {
-        if (a16) {  // the warp-specialised form (same bits, about 2.5 % faster)
-            auto wk = nonosc ? (lid ? k_fused_ws<true, true> : k_fused_ws<true, false>)
-                             : (lid ? k_fused_ws<false, true> : k_fused_ws<false, false>);
-            const size_t wsmem = (size_t)39 * L::PL * sizeof(float);
-            e = cudaFuncSetAttribute(wk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wsmem);
-            if (e != cudaSuccess) return e;
-            wk<<<ntx * nty, 640, wsmem, s>>>(a);
-            return cudaGetLastError();
-        }
-    }
-    kern<<<ntx * nty, nthreads, smem, s>>>(a);
+    const TileArgs a = tile_args(g, eps, TX, 0, h, psi, u1, u2, u3, out);
+    const int nty = (g.ny + TY - 1) / TY;
+    kern<<<a.ntx * nty, pairs_threads<TX, TY>(ld), smem, s>>>(a);
     return cudaGetLastError();
 }
 
-template <int TX, int TY>
+template <int TX, int TY, bool LD>
 cudaError_t launch_pairs_batch(int nonosc, int lid, const BatchGrid *grids, const int2 *items,
                                const int *begin, int ncta, int parity, cudaStream_t s) {
-    using L = Lay2<TX, TY, 4>;  // the two-column kernel's 4-plane ring
-    const size_t smem = (size_t)L::NPLANES * L::PL * sizeof(float);
-    auto kern = nonosc ? (lid ? k_fused_pairs_batch<TX, TY, true, true> : k_fused_pairs_batch<TX, TY, true, false>)
-                       : (lid ? k_fused_pairs_batch<TX, TY, false, true> : k_fused_pairs_batch<TX, TY, false, false>);
+    const size_t smem = pairs_smem<TX, TY>();
+    auto kern = nonosc ? (lid ? k_fused_pairs_batch<TX, TY, true, true, LD> : k_fused_pairs_batch<TX, TY, true, false, LD>)
+                       : (lid ? k_fused_pairs_batch<TX, TY, false, true, LD> : k_fused_pairs_batch<TX, TY, false, false, LD>);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    kern<<<ncta, L::NT, smem, s>>>(grids, items, begin, parity);
+    kern<<<ncta, pairs_threads<TX, TY>(LD), smem, s>>>(grids, items, begin, parity);
+    return cudaGetLastError();
+}
+
+template <int TX, int TY, bool LD>
+cudaError_t launch_pairs_direct(int nonosc, int lid, const DirectBatch &d, int parity, cudaStream_t s) {
+    const size_t smem = pairs_smem<TX, TY>();
+    auto kern = nonosc ? (lid ? k_fused_pairs_direct<TX, TY, true, true, LD> : k_fused_pairs_direct<TX, TY, true, false, LD>)
+                       : (lid ? k_fused_pairs_direct<TX, TY, false, true, LD> : k_fused_pairs_direct<TX, TY, false, false, LD>);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<d.start[d.nruns], pairs_threads<TX, TY>(LD), smem, s>>>(d, parity);
     return cudaGetLastError();
 }
 
@@ -1185,8 +796,8 @@ cudaError_t launch_pairs_batch(int nonosc, int lid, const BatchGrid *grids, cons
 
 bool fused_pairs_supported(const Grid &g, int tx, int ty) {
     (void)g;  // any nx: 16-byte loads when nx % 4 == 0, 4-byte loads otherwise
-    // 16 and 24 rows: 360 / 504 threads at up to 128 registers; 28 rows: 576
-    // threads (18 warps) at 96 registers, which hides latency better
+    // 16 rows: 360 threads at up to 128 registers; 24 and 28 rows with
+    // nx % 4 == 0: 16 / 18 compute warps and two loader warps at 96
     return tx == 32 && (ty == 16 || ty == 24 || ty == 28);
 }
 
@@ -1203,90 +814,47 @@ cudaError_t launch_fused_bands(const Grid &g, int nonosc, double eps, const Band
                                const void *psi, const void *u1, const void *u2, const void *u3,
                                void *out, cudaStream_t s, cudaStream_t s2, cudaEvent_t ev_fork,
                                cudaEvent_t ev_join) {
-    using L28 = Lay2<32, 28, 4>;
-    using L24 = Lay2<32, 24>;
     if (g.nx % 4 != 0 || plan.n28 < 1 || plan.n24 < 1) return cudaErrorInvalidValue;
     const bool lid = !g.per[0] || !g.per[1];
-    auto k28 = nonosc ? (lid ? k_fused_pairs<32, 28, true, true, 1, true> : k_fused_pairs<32, 28, true, false, 1, true>)
-                      : (lid ? k_fused_pairs<32, 28, false, true, 1, true> : k_fused_pairs<32, 28, false, false, 1, true>);
-    auto k24 = nonosc ? (lid ? k_fused_ws<true, true> : k_fused_ws<true, false>)
-                      : (lid ? k_fused_ws<false, true> : k_fused_ws<false, false>);
-    const size_t sm28 = (size_t)L28::NPLANES * L28::PL * sizeof(float);
-    const int nt28 = L28::NT + 64;  // with the two loader warps
-    const size_t sm24 = (size_t)39 * L24::PL * sizeof(float);
+    const SingleKernel k28 = single_kernel<32, 28, 1, true>(nonosc, lid);
+    const SingleKernel k24 = single_kernel<32, 24, 1, true>(nonosc, lid);
+    const size_t sm28 = pairs_smem<32, 28>(), sm24 = pairs_smem<32, 24>();
     cudaError_t e = cudaFuncSetAttribute(k28, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm28);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k24, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm24);
     if (e == cudaSuccess) e = cudaEventRecord(ev_fork, s);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(s2, ev_fork, 0);
     if (e != cudaSuccess) return e;
-    TileArgs a;
-    a.g = g;
-    a.ntx = (g.nx + 31) / 32;
-    a.eps = (float)eps;
-    a.h = (const float *)h; a.psi = (const float *)psi; a.u1 = (const float *)u1;
-    a.u2 = (const float *)u2; a.u3 = (const float *)u3; a.out = (float *)out;
-    a.y0 = 0;
-    k28<<<a.ntx * plan.n28, nt28, sm28, s>>>(a);
+    TileArgs a = tile_args(g, eps, 32, 0, h, psi, u1, u2, u3, out);
+    k28<<<a.ntx * plan.n28, pairs_threads<32, 28>(true), sm28, s>>>(a);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     a.y0 = 28 * plan.n28;
-    k24<<<a.ntx * plan.n24, 640, sm24, s2>>>(a);
+    k24<<<a.ntx * plan.n24, pairs_threads<32, 24>(true), sm24, s2>>>(a);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     e = cudaEventRecord(ev_join, s2);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ev_join, 0);
     return e;
 }
 
-cudaError_t launch_fused_ws_batch(int nonosc, int lid, const BatchGrid *grids, const int2 *items,
-                                  const int *begin, int ncta, int parity, cudaStream_t s) {
-    using L = Lay2<32, 24>;
-    const size_t smem = (size_t)39 * L::PL * sizeof(float);
-    auto kern = nonosc ? (lid ? k_fused_ws_batch<true, true> : k_fused_ws_batch<true, false>)
-                       : (lid ? k_fused_ws_batch<false, true> : k_fused_ws_batch<false, false>);
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    kern<<<ncta, 640, smem, s>>>(grids, items, begin, parity);
-    return cudaGetLastError();
-}
-
-template <int TX, int TY>
-cudaError_t launch_pairs_direct(int nonosc, int lid, const DirectBatch &d, int parity, cudaStream_t s) {
-    using L = Lay2<TX, TY, 4>;
-    const size_t smem = (size_t)L::NPLANES * L::PL * sizeof(float);
-    auto kern = nonosc ? (lid ? k_fused_pairs_direct<TX, TY, true, true> : k_fused_pairs_direct<TX, TY, true, false>)
-                       : (lid ? k_fused_pairs_direct<TX, TY, false, true> : k_fused_pairs_direct<TX, TY, false, false>);
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    kern<<<d.start[d.nruns], L::NT, smem, s>>>(d, parity);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_fused_pairs_direct(int ty, int nonosc, int lid, const DirectBatch &d, int parity,
-                                      cudaStream_t s) {
-    if (d.nruns < 1 || d.nruns > kDirectMaxRuns || d.start[d.nruns] < 1) return cudaErrorInvalidValue;
-    if (ty == 16) return launch_pairs_direct<32, 16>(nonosc, lid, d, parity, s);
-    if (ty == 24) return launch_pairs_direct<32, 24>(nonosc, lid, d, parity, s);
-    if (ty == 28) return launch_pairs_direct<32, 28>(nonosc, lid, d, parity, s);
+cudaError_t launch_fused_pairs_batch(int tx, int ty, int ld, int nonosc, int lid, const BatchGrid *grids,
+                                     const int2 *items, const int *begin, int ncta, int parity,
+                                     cudaStream_t s) {
+    if (tx != 32) return cudaErrorInvalidValue;
+    if (ty == 16 && !ld) return launch_pairs_batch<32, 16, false>(nonosc, lid, grids, items, begin, ncta, parity, s);
+    if (ty == 24) return ld ? launch_pairs_batch<32, 24, true>(nonosc, lid, grids, items, begin, ncta, parity, s)
+                            : launch_pairs_batch<32, 24, false>(nonosc, lid, grids, items, begin, ncta, parity, s);
+    if (ty == 28) return ld ? launch_pairs_batch<32, 28, true>(nonosc, lid, grids, items, begin, ncta, parity, s)
+                            : launch_pairs_batch<32, 28, false>(nonosc, lid, grids, items, begin, ncta, parity, s);
     return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_fused_ws_direct(int nonosc, int lid, const DirectBatch &d, int parity, cudaStream_t s) {
+cudaError_t launch_fused_pairs_direct(int ty, int ld, int nonosc, int lid, const DirectBatch &d, int parity,
+                                      cudaStream_t s) {
     if (d.nruns < 1 || d.nruns > kDirectMaxRuns || d.start[d.nruns] < 1) return cudaErrorInvalidValue;
-    using L = Lay2<32, 24>;
-    const size_t smem = (size_t)39 * L::PL * sizeof(float);
-    auto kern = nonosc ? (lid ? k_fused_ws_direct<true, true> : k_fused_ws_direct<true, false>)
-                       : (lid ? k_fused_ws_direct<false, true> : k_fused_ws_direct<false, false>);
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    kern<<<d.start[d.nruns], 640, smem, s>>>(d, parity);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_fused_pairs_batch(int tx, int ty, int nonosc, int lid, const BatchGrid *grids,
-                                     const int2 *items, const int *begin, int ncta, int parity,
-                                     cudaStream_t s) {
-    if (tx == 32 && ty == 16) return launch_pairs_batch<32, 16>(nonosc, lid, grids, items, begin, ncta, parity, s);
-    if (tx == 32 && ty == 24) return launch_pairs_batch<32, 24>(nonosc, lid, grids, items, begin, ncta, parity, s);
-    if (tx == 32 && ty == 28) return launch_pairs_batch<32, 28>(nonosc, lid, grids, items, begin, ncta, parity, s);
+    if (ty == 16 && !ld) return launch_pairs_direct<32, 16, false>(nonosc, lid, d, parity, s);
+    if (ty == 24) return ld ? launch_pairs_direct<32, 24, true>(nonosc, lid, d, parity, s)
+                            : launch_pairs_direct<32, 24, false>(nonosc, lid, d, parity, s);
+    if (ty == 28) return ld ? launch_pairs_direct<32, 28, true>(nonosc, lid, d, parity, s)
+                            : launch_pairs_direct<32, 28, false>(nonosc, lid, d, parity, s);
     return cudaErrorInvalidValue;
 }
 

@@ -94,9 +94,9 @@ cudaError_t launch_stage_step(int dtype, const Grid &g, int iterations, int nono
                               const void *u1, const void *u2, const void *u3, void *out,
                               const StageBuffers &b, cudaStream_t s);
 
-// Fused step.  FP32 grids with nx % 4 == 0 and a pair tile (32x16, 32x24)
-// run the two-columns-per-thread kernel (mpdata_fused2.cu); everything else
-// runs the one-column kernel (mpdata_fused.cu).  Returns
+// Fused step.  FP32 grids with a pair tile (32x16, 32x24, 32x28) run the
+// two-columns-per-thread kernel (mpdata_fused2.cu); everything else runs the
+// one-column kernel (mpdata_fused.cu).  Returns
 // cudaErrorInvalidValue for a tile shape with no compiled instance.
 cudaError_t launch_fused_step(int dtype, const Grid &g, int nonosc, double eps, int tile_x,
                               int tile_y, const void *h, const void *psi, const void *u1,
@@ -106,16 +106,14 @@ bool fused_tile_supported(int dtype, const Grid &g, int tile_x, int tile_y);
 void fused_default_tile(int dtype, const Grid &g, int nsm, int *tile_x, int *tile_y);
 bool fused_pairs_supported(const Grid &g, int tile_x, int tile_y);
 // Persistent batched launches (ncta CTAs; CTA c runs items [begin[c], begin[c+1])).
-cudaError_t launch_fused_pairs_batch(int tile_x, int tile_y, int nonosc, int lid,
+// ld: every grid of the launch has nx % 4 == 0 and the tile (24 or 28 rows)
+// takes the two loader warps; tile_y 16 runs without them.
+cudaError_t launch_fused_pairs_batch(int tile_x, int tile_y, int ld, int nonosc, int lid,
                                      const BatchGrid *grids, const int2 *items, const int *begin,
                                      int ncta, int parity, cudaStream_t s);
-// The same with the warp-specialised 32x24 kernel (grids with nx % 4 == 0).
-cudaError_t launch_fused_ws_batch(int nonosc, int lid, const BatchGrid *grids, const int2 *items,
-                                  const int *begin, int ncta, int parity, cudaStream_t s);
 // One CTA per item, grid table in the parameters (d.start[d.nruns] CTAs).
-cudaError_t launch_fused_pairs_direct(int tile_y, int nonosc, int lid, const DirectBatch &d, int parity,
-                                      cudaStream_t s);
-cudaError_t launch_fused_ws_direct(int nonosc, int lid, const DirectBatch &d, int parity, cudaStream_t s);
+cudaError_t launch_fused_pairs_direct(int tile_y, int ld, int nonosc, int lid, const DirectBatch &d,
+                                      int parity, cudaStream_t s);
 cudaError_t launch_fused_pairs(const Grid &g, int nonosc, double eps, int tile_x, int tile_y,
                                const void *h, const void *psi, const void *u1, const void *u2,
                                const void *u3, void *out, cudaStream_t s);

@@ -301,7 +301,7 @@ cudaError_t run_tick(mpdata_server *s, const std::vector<Request *> &act, int ch
         for (int st = 0; st < chunk && e == cudaSuccess; ++st)
             for (int v = 0; v < kNumVariants && e == cudaSuccess; ++v)
                 if (ncta[v])
-                    e = mpdata::launch_fused_pairs_direct(s->o.tile_y, s->o.nonoscillatory, v == kPairsLid,
+                    e = mpdata::launch_fused_pairs_direct(s->o.tile_y, 0, s->o.nonoscillatory, v == kPairsLid,
                                                           *direct[v], st & 1, s->stream);
     } else {
         e = ensure(&T.d_grids, &T.cap_grids, (size_t)na, s->stream);
@@ -317,7 +317,7 @@ cudaError_t run_tick(mpdata_server *s, const std::vector<Request *> &act, int ch
             for (int v = 0; v < kNumVariants && e == cudaSuccess; ++v) {
                 if (!ncta[v]) continue;
                 const int *begin = T.d_begin + voff[v];
-                e = mpdata::launch_fused_pairs_batch(32, s->o.tile_y, s->o.nonoscillatory, v == kPairsLid,
+                e = mpdata::launch_fused_pairs_batch(32, s->o.tile_y, 0, s->o.nonoscillatory, v == kPairsLid,
                                                          T.d_grids, T.d_items, begin, ncta[v], parity, s->stream);
             }
         }

@@ -5,7 +5,7 @@ import math
 
 import pytest
 
-T28, T24 = 1.96, 1.76  # us per plane of one CTA: 32x28 two-column, 32x24 warp-specialised
+T28, T24 = 1.95, 1.69  # us per plane of one CTA: 32x28 and 32x24, two-column with loader warps
 
 
 def handout(costs, nsm):

@@ -143,8 +143,10 @@ def test_per_grid_tiles(mp, graph):
         want = []
         for i, (f, ty) in enumerate(zip(fs, tiles)):
             lid = not (f.periodic[0] and f.periodic[1])
-            if (ty or 24) == 24 and f.nx % 4 == 0:  # warp-specialised 32x24
+            if (ty or 24) == 24 and f.nx % 4 == 0:  # 32x24 with loader warps
                 want.append(7 if lid else 2)
+            elif ty == 28 and f.nx % 4 == 0:  # 32x28 with loader warps
+                want.append(9 if lid else 8)
             else:
                 want.append({24: 0, 16: 3, 28: 5}[ty or 24] + int(lid))
         assert [b.grid_variant(i) for i in range(len(fs))] == want

@@ -1,7 +1,7 @@
 """The headline configuration checked cell by cell: the 1024x512x64
 rotation-blob grid (periodic x/y, lids in z) run by the production launch --
-the default tile, i.e. row bands of 32x28 and warp-specialised 32x24 tiles as
-two concurrent launches -- for 10 steps against the FP64 oracle on every
+the default tile, i.e. row bands of 32x28 and 32x24 tiles (both with loader
+warps) as two concurrent launches -- for 10 steps against the FP64 oracle on every
 cell (max |dpsi| <= 1e-5 max|psi|)."""
 import numpy as np
 import pytest

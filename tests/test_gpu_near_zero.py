@@ -5,7 +5,7 @@ The limiter's ratios A, B and beta divide by sums of psi plus eps; on a
 itself (1e-15).  This is where FP32 state, the hardware reciprocal and the
 FP32 beta factors of the fused kernels could go wrong, so every fused kernel
 form runs here: the default tile of a small grid (one-column kernel), the
-two-column 32x28 tile, the warp-specialised 32x24 tile and the row-band
+two-column 32x28 and 32x24 tiles (loader warps) and the row-band
 launch of a 1024x512 grid (both tile heights at once).  Checked element by
 element against the oracle (max |dpsi| <= 1e-5 max|psi| after 10 steps,
 <= 1e-4 after 100), with the scheme's invariants: psi stays >= 0
