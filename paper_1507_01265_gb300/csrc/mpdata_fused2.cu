@@ -495,7 +495,7 @@ __device__ __forceinline__ void pairs_tile(const TileArgs &a, int tile, float *s
             const F2 gxr = rshF(tb + oGX, gx_own), gyu = ldp<oGY + RB>(tb);
             dacc = add(add(sub(gxr, gx_own), sub(gyu, gy_own)), dacc);
         }
-        F2 sxc = sxb, syc = syb, v1_own = Z, v2_own = Z, pl = Z, pd = Z;
+        F2 sxc = sxb, syc = syb, v1_own = Z, v2_own = Z, pl = Z, pd = Z, u1R = Z, u2U = Z;
         if (!E || (q1 >= q1lo && q1 <= q1top)) {
             sxc = add(lshC(b1 + oP1, p1c), p1c);
             syc = add(ldp<oP1 - RB>(b1), p1c);
@@ -508,7 +508,7 @@ __device__ __forceinline__ void pairs_tile(const TileArgs &a, int tile, float *s
             pl = lshF(b2 + oP1, p1b);
             pd = ldp<oP1 - RB>(b2);
             {
-                const F2 u2U = ldp<2 * FB + RB>(r2);
+                u2U = ldp<2 * FB + RB>(r2);
                 const F2 ua = add(add(add(lshF(r2 + 2 * FB, u2b), u2b),
                                       make_float2(lds<2 * FB + RB - 4>(r2), u2U.x)), u2U);
                 const F2 ub = add(add(add(lshF(r2 + 3 * FB, u3b), u3b), lshF(r1 + 3 * FB, u3c)), u3c);
@@ -519,8 +519,8 @@ __device__ __forceinline__ void pairs_tile(const TileArgs &a, int tile, float *s
             {
                 const F2 u1D = ldp<FB - RB>(r2);
                 const F2 va = add(add(add(ldp<3 * FB - RB>(r2), u3b), ldp<3 * FB - RB>(r1)), u3c);
-                const F2 vb = add(add(add(u1D, u1b), make_float2(u1D.y, lds<FB - RB + 8>(r2))),
-                                  rshF(r2 + FB, u1b));
+                u1R = rshF(r2 + FB, u1b);
+                const F2 vb = add(add(add(u1D, u1b), make_float2(u1D.y, lds<FB - RB + 8>(r2))), u1R);
                 const F2 v = pseudo_velocity(u2b, p1b, pd, syb, syc, sya, va, rshC(b2 + oSY, syb),
                                              lshC(b2 + oSY, syb), vb, add(ldp<4 * FB - RB>(r2), hb), eps);
                 v2_own = (LID && ylid) ? Z : v;
@@ -535,15 +535,22 @@ __device__ __forceinline__ void pairs_tile(const TileArgs &a, int tile, float *s
         if (in_beta) {
             if (!E || (q2 >= wlo && q2 <= whi)) {
                 const F2 szo = add(p1b, p1c);
-                const F2 ua = add(add(add(u1b, u1c), rshF(r2 + FB, u1b)), rshF(r1 + FB, u1c));
-                const F2 ub = add(add(add(u2b, u2c), ldp<2 * FB + RB>(r2)), ldp<2 * FB + RB>(r1));
+                // the x/y pseudo-velocities (same z range when E is false) read
+                // u1 right of the pair and u2 above it already
+                const F2 u1R2 = !E ? u1R : rshF(r2 + FB, u1b);
+                const F2 u2U2 = !E ? u2U : ldp<2 * FB + RB>(r2);
+                const F2 ua = add(add(add(u1b, u1c), u1R2), rshF(r1 + FB, u1c));
+                const F2 ub = add(add(add(u2b, u2c), u2U2), ldp<2 * FB + RB>(r1));
                 whi_v = pseudo_velocity(u3c, p1c, p1b, szo, rshC(tb + oSZ, szo), lshC(tb + oSZ, szo), ua,
                                         ldU(tb + oSZ), ldD(tb + oSZ), ub, add(hb, hc), eps);
             }
             if (NONOSC && (!E || (q2 >= vlo && q2 <= vhi))) {
                 const F2 aL = lshC(r2, pn_m), aR = rshC(r2, pn_m), aD = ldD(r2), aU = ldU(r2);
-                const F2 bL = lshC(b2 + oP1, p1b), bR = rshC(b2 + oP1, p1b);
-                const F2 bD = ldD(b2 + oP1), bU = ldU(b2 + oP1);
+                // psi1's left and lower neighbours: pl and pd of the alpha phase
+                // (same z range), clamped behind a lid
+                const F2 bL = LID ? make_float2(clampL ? p1b.x : pl.x, p1b.x) : pl;
+                const F2 bD = (LID && dD == 0) ? p1b : pd;
+                const F2 bR = rshC(b2 + oP1, p1b), bU = ldU(b2 + oP1);
                 F2 mx = max3(max3(aL, aR, aD), max3(aU, bL, bR), max3(bD, bU, pn_mm));
                 mx = max3(mx, max3(pn_m, pn_c, p1a), max3(p1b, p1c, p1b));
                 F2 mn = min3(min3(aL, aR, aD), min3(aU, bL, bR), min3(bD, bU, pn_mm));
