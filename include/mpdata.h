@@ -82,11 +82,12 @@ typedef struct mpdata_opts {
     int32_t periodic[3];    /* per axis x, y, z: 1 periodic (default), 0 rigid lid */
     int32_t dtype;          /* MPDATA_F32 (default) or MPDATA_F64 */
     int32_t path;           /* MPDATA_PATH_FUSED (default) or MPDATA_PATH_STAGES */
-    int32_t tile_x, tile_y; /* fused-kernel output tile.  FP32: 32x28, 32x24 or 32x16 run the
-                               two-column kernel (any nx), 24x24, 24x16, 16x16 the
-                               one-column kernel; FP64: 16x16.  0 x 0 picks the tile
-                               of least predicted step time for the grid on this
-                               device (waves of tiles x measured per-plane time) */
+    int32_t tile_x, tile_y; /* fused-kernel output tile.  FP32: 32x28, 32x24, 32x16 or
+                               32x12 (two CTAs per SM) run the two-column kernel
+                               (any nx), 24x24, 24x16, 16x16 the one-column kernel;
+                               FP64: 16x16.  0 x 0 picks the tile of least
+                               predicted step time for the grid on this device
+                               (waves of tiles x measured per-plane time) */
     double eps;             /* > 0, added to every A, B and limiter denominator; default 1e-15 */
     int32_t extrema;        /* MPDATA_EXTREMA_BOTH (default) or _CORRECTED (stage path) */
     int32_t precision;      /* MPDATA_PREC_PURE (default) or _F64_BETA (FP32, stage path) */

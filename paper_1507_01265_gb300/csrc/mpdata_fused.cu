@@ -435,26 +435,31 @@ bool fused_tile_supported(int dtype, const Grid &g, int tx, int ty) {
 void fused_default_tile(int dtype, const Grid &g, int nsm, int *tx, int *ty) {
     if (dtype == MPDATA_F64) { *tx = 16; *ty = 16; return; }
     // FP32: the tile of least predicted step time, waves x per-plane time of
-    // one CTA, waves = ceil(tiles / SMs) (one CTA per SM).  Per-plane times
+    // a wave, waves = ceil(tiles / (SMs x CTAs per SM)).  Per-plane times
     // measured on GB300 (us, nz 33..63): a small grid (one wave) wants the
     // smallest, fastest plane; a large one the most cells per plane-time.
-    struct Cand { int tx, ty; double us_aligned, us_any; };
+    // A tile of two CTAs per SM runs alone on its SM while the tiles do not
+    // outnumber the SMs (us_one), two to an SM beyond (us per wave).
+    struct Cand { int tx, ty, per_sm; double us_aligned, us_any, us_one_aligned, us_one_any; };
     static const Cand cands[] = {
-        // two-column kernel; with nx % 4 == 0 (16-byte loads) the 32x24 and
-        // 32x28 tiles add two loader warps to their 16 / 18 compute warps.
-        // Medians over serving-size grids with at most one tile per SM: step
-        // time / (nz + 6)
-        {32, 24, 1.69, 1.90},
-        {32, 28, 1.95, 2.49},
-        {32, 16, 1.40, 1.47},
-        {24, 16, 1.76, 1.77},  // one-column kernel
-        {16, 16, 1.45, 1.45},
+        // two-column kernel; with nx % 4 == 0 (16-byte loads) the 32x12, 32x24
+        // and 32x28 tiles add loader warps to their compute warps.  Medians
+        // over serving-size grids: step time / (nz + 6)
+        {32, 28, 1, 1.91, 2.38, 1.91, 2.38},
+        {32, 24, 1, 1.67, 1.91, 1.67, 1.91},
+        {32, 16, 1, 1.39, 1.45, 1.39, 1.45},
+        {32, 12, 2, 1.78, 2.25, 1.11, 1.76},  // 9 compute warps + 1 loader warp, two CTAs per SM
+        {24, 16, 1, 1.76, 1.76, 1.76, 1.76},  // one-column kernel
+        {16, 16, 1, 1.44, 1.45, 1.44, 1.45},
     };
-    const int sms = nsm > 0 ? nsm : 1 << 30;  // unknown device: every grid is one wave
+    const int sms = nsm > 0 ? nsm : 1 << 28;  // unknown device: every grid is one wave
+    const bool a16 = g.nx % 4 == 0;
     double best = 0.0;
     for (const Cand &c : cands) {
         const long long tiles = (long long)((g.nx + c.tx - 1) / c.tx) * ((g.ny + c.ty - 1) / c.ty);
-        const double t = (double)((tiles + sms - 1) / sms) * (g.nx % 4 == 0 ? c.us_aligned : c.us_any);
+        const long long slots = (long long)sms * c.per_sm;
+        const double t = tiles <= sms ? (a16 ? c.us_one_aligned : c.us_one_any)
+                                      : (double)((tiles + slots - 1) / slots) * (a16 ? c.us_aligned : c.us_any);
         if (best == 0.0 || t < best * 0.98) { best = t; *tx = c.tx; *ty = c.ty; }
     }
 }
@@ -492,7 +497,7 @@ bool fused_band_plan(const Grid &g, int nsm, BandPlan *plan) {
     // one tile height would leave a mostly empty band.  Per-plane times as in
     // fused_default_tile; 0.02 x the 28-row plane time covers the fork and the
     // join.
-    const double t28 = 1.95, t24 = 1.69;
+    const double t28 = 1.91, t24 = 1.67;
     if (nsm <= 0 || g.nx % 4 != 0) return false;
     const long long ntx = (g.nx + 31) / 32;
     const long long w24 = (ntx * ((g.ny + 23) / 24) + nsm - 1) / nsm, w28 = (ntx * ((g.ny + 27) / 28) + nsm - 1) / nsm;

@@ -1,6 +1,6 @@
 // Fused MPDATA step, FP32, two adjacent x-columns per thread.
 //
-// A CTA marches a TX x TY tile through z (TX = 32; TY = 16, 24 or 28).  Per
+// A CTA marches a TX x TY tile through z (TX = 32; TY = 12, 16, 24 or 28).  Per
 // iteration p, with q1 = p-1, q2 = p-2, q3 = p-3, three barriers:
 //   alpha  donor pass of q1 completed from the neighbours' fluxes (a1), pair
 //          sums for the cross terms, x/y pseudo-velocities at q2 (a2);
@@ -30,9 +30,11 @@
 // Threads are numbered from the tile outwards ring by ring in pair units, so
 // each stage's region is a prefix of the thread index.
 // The 32x24 and 32x28 tiles of a grid with nx % 4 == 0 add two loader warps
-// to their 16 / 18 compute warps (pairs_loader): they issue and wait for
-// every input load, so the compute threads hold no load state (fewer spills)
-// and no load instructions.
+// to their 16 / 18 compute warps, the 32x12 tile one to its 9 (pairs_loader):
+// they issue and wait for every input load, so the compute threads hold no
+// load state (fewer spills) and no load instructions.  The 32x12 tile's
+// 104 KB of shared memory let two CTAs share an SM, so that one CTA's warps
+// run while the other's wait at a barrier.
 #include <type_traits>
 
 #include "mpdata_internal.cuh"
@@ -113,6 +115,8 @@ __device__ __forceinline__ F2 pseudo_velocity(F2 U, F2 pR, F2 pL, F2 psum, F2 sp
 // evict the kernel's spill lines).
 template <int TX, int TY, int NR_ = 5>
 struct Lay2 {
+    static constexpr int NLD = TY == 12 ? 32 : 64;  // loader threads (with loader warps)
+    static constexpr int MINB = TY == 12 ? 2 : 1;   // CTAs per SM
     static_assert(TX % 4 == 0, "TX must be a multiple of 4");
     static constexpr int HX = TX / 2;           // output pairs per row
     static constexpr int NPX = HX + 2;          // pairs of the radius-2 regions
@@ -229,7 +233,7 @@ using BF = std::integral_constant<bool, false>;
 template <int TX, int TY, bool LID>
 __device__ __forceinline__ void pairs_loader(const TileArgs &a, int tile, float *sm) {
     using L = Lay2<TX, TY, 4>;
-    constexpr int NLD = 64;
+    constexpr int NLD = L::NLD;
     constexpr int KCH = (L::NCH + NLD - 1) / NLD;
     static_assert(KCH <= 8, "chunk flags are packed 8 per byte");
     constexpr int PL = L::PL, PB = PL * 4, FB = L::NR * PB, EX = L::EX;
@@ -674,7 +678,8 @@ __device__ __forceinline__ void pairs_tile(const TileArgs &a, int tile, float *s
 }
 
 template <int TX, int TY, bool NONOSC, bool LID, int AL, bool LD = false>
-__global__ void __launch_bounds__(LD ? Lay2<TX, TY>::NTW + 64 : Lay2<TX, TY>::NT, 1) k_fused_pairs(TileArgs a) {
+__global__ void __launch_bounds__(LD ? Lay2<TX, TY>::NTW + Lay2<TX, TY>::NLD : Lay2<TX, TY>::NT, Lay2<TX, TY>::MINB)
+    k_fused_pairs(TileArgs a) {
     extern __shared__ __align__(16) float sm[];
     pairs_tile<TX, TY, NONOSC, LID, AL, LD>(a, blockIdx.x, sm);
 }
@@ -683,7 +688,7 @@ __global__ void __launch_bounds__(LD ? Lay2<TX, TY>::NTW + 64 : Lay2<TX, TY>::NT
 // the item list, each item a (grid, tile) pair; parity selects which buffer
 // of each grid's (psi, scratch) pair is read.
 template <int TX, int TY, bool NONOSC, bool LID, bool LD = false>
-__global__ void __launch_bounds__(LD ? Lay2<TX, TY>::NTW + 64 : Lay2<TX, TY>::NT, 1)
+__global__ void __launch_bounds__(LD ? Lay2<TX, TY>::NTW + Lay2<TX, TY>::NLD : Lay2<TX, TY>::NT, 1)
     k_fused_pairs_batch(const BatchGrid *__restrict__ grids, const int2 *__restrict__ items,
                         const int *__restrict__ begin, int parity) {
     extern __shared__ __align__(16) float sm[];
@@ -707,7 +712,7 @@ __device__ __forceinline__ int direct_run(const DirectBatch &d, int c) {
 }
 
 template <int TX, int TY, bool NONOSC, bool LID, bool LD = false>
-__global__ void __launch_bounds__(LD ? Lay2<TX, TY>::NTW + 64 : Lay2<TX, TY>::NT, 1)
+__global__ void __launch_bounds__(LD ? Lay2<TX, TY>::NTW + Lay2<TX, TY>::NLD : Lay2<TX, TY>::NT, 1)
     k_fused_pairs_direct(const __grid_constant__ DirectBatch d, int parity) {
     extern __shared__ __align__(16) float sm[];
     const int c = blockIdx.x, r = direct_run(d, c);
@@ -718,10 +723,10 @@ __global__ void __launch_bounds__(LD ? Lay2<TX, TY>::NTW + 64 : Lay2<TX, TY>::NT
 // nx % 4 == 0 (16-byte loads); 16-row tiles and any other nx keep the
 // compute threads' own loads.
 template <int TY>
-constexpr bool has_loaders() { return TY == 24 || TY == 28; }
+constexpr bool has_loaders() { return TY == 12 || TY == 24 || TY == 28; }
 
 template <int TX, int TY>
-constexpr int pairs_threads(bool ld) { return ld ? Lay2<TX, TY>::NTW + 64 : Lay2<TX, TY>::NT; }
+constexpr int pairs_threads(bool ld) { return ld ? Lay2<TX, TY>::NTW + Lay2<TX, TY>::NLD : Lay2<TX, TY>::NT; }
 
 template <int TX, int TY>
 constexpr size_t pairs_smem() {  // the two-column kernel's 4-plane ring
@@ -769,6 +774,8 @@ cudaError_t launch_pairs(const Grid &g, int nonosc, double eps, const void *h, c
     bool ld;
     const SingleKernel kern = pick_single<TX, TY>(g, nonosc, ld);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess && Lay2<TX, TY>::MINB > 1)  // room for MINB CTAs per SM
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     if (e != cudaSuccess) return e;
     const TileArgs a = tile_args(g, eps, TX, 0, h, psi, u1, u2, u3, out);
     const int nty = (g.ny + TY - 1) / TY;
@@ -805,12 +812,13 @@ bool fused_pairs_supported(const Grid &g, int tx, int ty) {
     (void)g;  // any nx: 16-byte loads when nx % 4 == 0, 4-byte loads otherwise
     // 16 rows: 360 threads at up to 128 registers; 24 and 28 rows with
     // nx % 4 == 0: 16 / 18 compute warps and two loader warps at 96
-    return tx == 32 && (ty == 16 || ty == 24 || ty == 28);
+    return tx == 32 && (ty == 12 || ty == 16 || ty == 24 || ty == 28);
 }
 
 cudaError_t launch_fused_pairs(const Grid &g, int nonosc, double eps, int tx, int ty, const void *h,
                                const void *psi, const void *u1, const void *u2, const void *u3,
                                void *out, cudaStream_t s) {
+    if (tx == 32 && ty == 12) return launch_pairs<32, 12>(g, nonosc, eps, h, psi, u1, u2, u3, out, s);
     if (tx == 32 && ty == 16) return launch_pairs<32, 16>(g, nonosc, eps, h, psi, u1, u2, u3, out, s);
     if (tx == 32 && ty == 24) return launch_pairs<32, 24>(g, nonosc, eps, h, psi, u1, u2, u3, out, s);
     if (tx == 32 && ty == 28) return launch_pairs<32, 28>(g, nonosc, eps, h, psi, u1, u2, u3, out, s);

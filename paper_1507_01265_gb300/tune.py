@@ -42,9 +42,6 @@ import numpy as np
 
 from . import Batch, fpm
 
-TILES = {(32, 24): (32, 24), (32, 16): (32, 16)}
-
-
 def _device_fields(nx, ny, nz, seed=11, periodic=(1, 1, 0)):
     import torch
     import gen.fields as F
@@ -191,7 +188,7 @@ def tune_grid(nx, ny, nz, periodic=(1, 1, 0), steps=10, tiles=((32, 28), (32, 24
     return report
 
 
-TILES = ((32, 28), (32, 24), (32, 16), (24, 24), (24, 16), (16, 16))
+PROBE_TILES = ((32, 28), (32, 24), (32, 16), (32, 12), (24, 24), (24, 16), (16, 16))
 
 
 def probe_grids(count=40, seed=1511):
@@ -209,7 +206,7 @@ def probe_grids(count=40, seed=1511):
     return out
 
 
-def tile_times(grids, tiles=TILES, steps=20):
+def tile_times(grids, tiles=PROBE_TILES, steps=20):
     """Microseconds per step of one mpdata_step launch per tile shape, for
     each (nx, ny, nz) (x/y periodic, lid z), plus the default tile the
     library picks."""

@@ -5,7 +5,7 @@ import math
 
 import pytest
 
-T28, T24 = 1.95, 1.69  # us per plane of one CTA: 32x28 and 32x24, two-column with loader warps
+T28, T24 = 1.91, 1.67  # us per plane of one CTA: 32x28 and 32x24, two-column with loader warps
 
 
 def handout(costs, nsm):

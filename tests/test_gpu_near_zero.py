@@ -4,8 +4,9 @@ The limiter's ratios A, B and beta divide by sums of psi plus eps; on a
 1e-6 background those sums are tiny, and where psi is exactly 0 they are eps
 itself (1e-15).  This is where FP32 state, the hardware reciprocal and the
 FP32 beta factors of the fused kernels could go wrong, so every fused kernel
-form runs here: the default tile of a small grid (one-column kernel), the
-two-column 32x28 and 32x24 tiles (loader warps) and the row-band
+form runs here: the default tile of a small grid (32x12, two CTAs per SM),
+the one-column 16x16 tile, the two-column 32x28 and 32x24 tiles (loader
+warps) and the row-band
 launch of a 1024x512 grid (both tile heights at once).  Checked element by
 element against the oracle (max |dpsi| <= 1e-5 max|psi| after 10 steps,
 <= 1e-4 after 100), with the scheme's invariants: psi stays >= 0
@@ -53,7 +54,7 @@ def check(f, got, want, nsteps):
 
 
 @pytest.mark.parametrize("nsteps", [10, 100])
-@pytest.mark.parametrize("tile", [None, (32, 28), (32, 24)])
+@pytest.mark.parametrize("tile", [None, (16, 16), (32, 28), (32, 24)])
 @pytest.mark.parametrize("kind", ["near_zero", "exact_zero"])
 def test_small_grid(kind, tile, nsteps):
     f = fields(kind, 128, 112, 16)

@@ -69,7 +69,7 @@ def test_edge_shapes_f64(nx, ny, nz, per, nonosc):
 
 
 @pytest.mark.parametrize("nx,ny,nz,per", EDGE)
-@pytest.mark.parametrize("tile", [None, (24, 24), (16, 16), (32, 16), (32, 24), (32, 28)])
+@pytest.mark.parametrize("tile", [None, (24, 24), (16, 16), (32, 12), (32, 16), (32, 24), (32, 28)])
 def test_edge_shapes_f32(nx, ny, nz, per, tile):
     f = rand_problem((nz, ny, nx), seed=nx * 17 + ny * 5 + nz, periodic=per)
     want = run_oracle(f, 3)
@@ -345,15 +345,17 @@ def test_courant_max_closed_forms():
 def test_default_tile_choice():
     """The default tile follows the predicted step time: the two-column
     kernel with 32x28 tiles for the 1024x512 grid (608 tiles, four full
-    waves on 152 SMs, against five of 32x24), 32x24 for 4096x2048 (73 waves
-    of 1.69 us per plane against 63 of 1.95: 32x28 is not the 2 % better
-    that displaces the first candidate), a tile of the fastest single-CTA
-    plane (32x16 two-column or 16x16 one-column, 1.40 and 1.45 us per
-    plane) for a grid too small to fill the GPU, 16x16 for FP64."""
+    waves on 152 SMs, against five of 32x24) and for 4096x2048 (63 waves of
+    1.91 us per plane against 73 of 1.67: 32x24 is not the 2 % better that
+    displaces the first candidate), the fastest single-CTA plane for a grid
+    too small to fill the GPU (32x12 with its loader warp, 1.11 us, when
+    nx % 4 == 0; else 32x16 or 16x16 at 1.45 each), 16x16 for FP64."""
     import torch
     import paper_1507_01265_gb300 as mp
     nsm = torch.cuda.get_device_properties(0).multi_processor_count
     with mp.Solver(40, 24, 12) as s:
+        assert s.tile == (32, 12)
+    with mp.Solver(42, 24, 12) as s:
         assert s.tile in ((16, 16), (32, 16))
     with mp.Solver(64, 64, 8, dtype="f64") as s:
         assert s.tile == (16, 16)
@@ -363,7 +365,7 @@ def test_default_tile_choice():
         with mp.Solver(1024, 512, 64, periodic=(1, 1, 0)) as s:
             assert s.tile == (32, 28)
         with mp.Solver(4096, 2048, 32, periodic=(1, 1, 0)) as s:
-            assert s.tile == (32, 24)
+            assert s.tile == (32, 28)
 
 
 @pytest.mark.parametrize("nonosc", [True, False])
@@ -417,7 +419,7 @@ def test_row_bands_in_a_cuda_graph():
     assert np.array_equal(t[1].double().cpu().numpy(), eager)
 
 
-@pytest.mark.parametrize("ty", [24, 28])
+@pytest.mark.parametrize("ty", [12, 24, 28])
 @pytest.mark.parametrize("nonosc", [True, False])
 @pytest.mark.parametrize("nx,ny,nz,per", [
     (96, 50, 9, (1, 1, 0)), (128, 61, 7, (1, 1, 1)), (64, 24, 33, (1, 1, 0)), (32, 5, 4, (1, 1, 1)),
@@ -425,17 +427,21 @@ def test_row_bands_in_a_cuda_graph():
     (4, 3, 2, (0, 0, 0)), (8, 52, 5, (1, 0, 0)),
 ])
 def test_loader_warp_tile(nx, ny, nz, per, nonosc, ty):
-    """32x24 and 32x28 tiles of grids with nx % 4 == 0 (lids on x or y
-    included) run the two-column kernel with two loader warps (the compute
+    """32x12, 32x24 and 32x28 tiles of grids with nx % 4 == 0 (lids on x or
+    y included) run the two-column kernel with loader warps (the compute
     warps issue no loads; the 32x24 tile's last compute warp carries 8 idle
-    threads).  It matches the oracle and, bit for bit, the batch's
+    threads; the 32x12 tile has one loader warp and two CTAs per SM).  It
+    matches the oracle and, bit for bit, the 32x28 tile and the batch's
     persistent kernel, whose CTAs run several tiles each and whose loader
-    warps therefore cross from tile to tile."""
+    warps therefore cross from tile to tile (24 and 28 rows)."""
     import torch
     import paper_1507_01265_gb300 as mp
     f = rand_problem((nz, ny, nx), seed=nx + ny + nz, periodic=per)
     got = run_gpu(f, 10, tile=(32, ty), nonosc=nonosc)
     assert rel_err(got, run_oracle(f, 10, nonosc=nonosc)) <= 1e-5
+    if ty == 12:
+        assert np.array_equal(got, run_gpu(f, 10, tile=(32, 28), nonosc=nonosc))
+        return
     t = [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in (f.h, f.psi, f.u1, f.u2, f.u3)]
     with mp.Batch([(nx, ny, nz, per)], tile=(32, ty), nonoscillatory=nonosc) as b:
         v = b.grid_variant(0)
