@@ -141,6 +141,15 @@ int mpdata_get_bands(const mpdata_t *handle, int *n28, int *n24);
  * considered for grids with nx % 4 == 0 and at most 48 waves of tiles.  Errors: EINVAL (NULL argument, dims < 1, nsm < 0). */
 int mpdata_plan_bands(int nx, int ny, int nz, const int *periodic, int nsm, int *n28, int *n24);
 
+/* The fused-kernel tile mpdata_create takes for an nx x ny x nz grid of dtype
+ * with tile_x = tile_y = 0 on a device of nsm SMs (host only, no device
+ * call; nsm = 0: a device of unknown size, every grid one wave): the tile of
+ * least predicted step time, ceil(tiles / (nsm x CTAs per SM)) waves x the
+ * tile's per-plane time measured on GB300 (one-wave time while the tiles do
+ * not outnumber the SMs).  The boundaries do not enter the choice.  Errors:
+ * EINVAL (NULL argument, dims < 1, nsm < 0, unknown dtype). */
+int mpdata_default_tile(int nx, int ny, int nz, int dtype, int nsm, int *tile_x, int *tile_y);
+
 /* Advance psi by nsteps MPDATA steps in place (async on `stream`): each
  * step reads the five fields and writes psi (§5.2); a run is a loop of such
  * steps (§6 times 40 of them).

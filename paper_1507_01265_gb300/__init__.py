@@ -33,6 +33,15 @@ def _stream_handle(stream):
     return ctypes.c_void_p(stream.cuda_stream)
 
 
+def default_tile(nx: int, ny: int, nz: int, dtype: str = "f32", nsm: int = 152):
+    """(tile_x, tile_y): the fused tile a default-tile solver of this grid
+    runs on a device of nsm SMs.  Host only."""
+    a, b = ctypes.c_int(), ctypes.c_int()
+    check(_lib.lib.mpdata_default_tile(int(nx), int(ny), int(nz), _DTYPES[dtype], int(nsm), ctypes.byref(a),
+                                       ctypes.byref(b)), "mpdata_default_tile")
+    return (a.value, b.value)
+
+
 def plan_bands(nx: int, ny: int, nz: int, periodic=(1, 1, 0), nsm: int = 152):
     """(n28, n24): the row bands a default-tile FP32 solver of this grid runs
     on a device of nsm SMs ((0, 0): one tile shape).  Host only."""

@@ -79,6 +79,7 @@ def _load():
         "mpdata_get_tile": (I, [H, ctypes.POINTER(I), ctypes.POINTER(I)]),
         "mpdata_get_bands": (I, [H, ctypes.POINTER(I), ctypes.POINTER(I)]),
         "mpdata_plan_bands": (I, [I, I, I, ctypes.POINTER(I), I, ctypes.POINTER(I), ctypes.POINTER(I)]),
+        "mpdata_default_tile": (I, [I, I, I, I, I, ctypes.POINTER(I), ctypes.POINTER(I)]),
         "mpdata_step": (I, [H, P, P, P, P, P, I, P]),
         "mpdata_solve_host": (I, [H, P, P, P, P, P, I, P]),
         "mpdata_host_submit": (I, [H, P, P, P, P, P, I, P, P, ctypes.POINTER(ctypes.c_ulonglong)]),

@@ -261,6 +261,17 @@ int mpdata_plan_bands(int nx, int ny, int nz, const int *periodic, int nsm, int 
     return MPDATA_OK;
 }
 
+int mpdata_default_tile(int nx, int ny, int nz, int dtype, int nsm, int *tile_x, int *tile_y) {
+    if (!tile_x || !tile_y) return fail(MPDATA_EINVAL, "NULL argument");
+    if (nx < 1 || ny < 1 || nz < 1 || nsm < 0) return fail(MPDATA_EINVAL, "bad dims or nsm");
+    if (dtype != MPDATA_F32 && dtype != MPDATA_F64) return fail(MPDATA_EINVAL, "dtype must be MPDATA_F32 or MPDATA_F64");
+    Grid g;
+    g.nx = nx; g.ny = ny; g.nz = nz;
+    for (int d = 0; d < 3; ++d) g.per[d] = 1;
+    mpdata::fused_default_tile(dtype, g, nsm, tile_x, tile_y);
+    return MPDATA_OK;
+}
+
 int mpdata_get_bands(const mpdata_t *m, int *n28, int *n24) {
     if (!m || !n28 || !n24) return fail(MPDATA_EINVAL, "NULL argument");
     *n28 = m->banded ? m->band.n28 : 0;

@@ -361,6 +361,9 @@ def test_default_tile_choice():
         assert s.tile == (16, 16)
     with mp.Solver(64, 64, 8, path="stages") as s:
         assert s.tile == (0, 0)
+    for nx, ny, nz in ((40, 24, 12), (42, 24, 12), (512, 256, 16), (1024, 512, 8), (300, 40, 4)):
+        with mp.Solver(nx, ny, nz, periodic=(1, 1, 0)) as s:
+            assert s.tile == mp.default_tile(nx, ny, nz, nsm=nsm), (nx, ny, nz)
     if nsm == 152:
         with mp.Solver(1024, 512, 64, periodic=(1, 1, 0)) as s:
             assert s.tile == (32, 28)
