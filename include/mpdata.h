@@ -305,7 +305,9 @@ int mpdata_batch_get_split(mpdata_batch_t *batch, int variant, int *begin);
  * split over min(ncta, nitems) CTAs: CTA c's last item is the one whose
  * cumulative cost is closest to (c+1)/ncta of the total. */
 int mpdata_batch_set_split(mpdata_batch_t *batch, int variant, int ncta, const int *begin);
-/* nsteps steps of every grid (async on stream).  use_graph != 0 captures the
+/* nsteps steps of every grid (async on stream; with several non-empty
+ * variants each variant's launches run on a stream of the batch that forks
+ * from and joins back into `stream`).  use_graph != 0 captures the
  * whole sequence once per nsteps into a CUDA graph and replays it (the graph
  * is rebuilt after set_fields or set_split).  Odd nsteps copies each psi to
  * its scratch first so that the result lands in psi. */

@@ -11,9 +11,11 @@
 // the next one; the balanced split (one CTA per SM, contiguous ranges of
 // nearly equal cost) and any other split, including the uneven ones of the
 // speed-function autotuner, can be installed instead.  A step of the batch is
-// one launch per variant; nsteps steps can be captured once into a CUDA graph
-// and replayed.  32x24 and 32x28 tiles of grids with nx % 4 == 0 run the
-// kernel with loader warps, as a single-grid launch with that tile does.  Each
+// one launch per variant (with several variants, each variant's launches run
+// on a stream of its own, concurrently with the others'); nsteps steps can be
+// captured once into a CUDA graph and replayed.  32x24 and 32x28 tiles of
+// grids with nx % 4 == 0 run the kernel with loader warps, as a single-grid
+// launch with that tile does.  Each
 // tile is computed by the same code whichever CTA runs it, so every grid's
 // result is bit-identical to the single-grid launch.
 #include <stdarg.h>
@@ -82,6 +84,12 @@ struct mpdata_batch {
     bool grids_dirty = true;
     Group group[kNumVariants];
     cudaStream_t capture_stream = nullptr;
+    // with several non-empty variants, each variant's chain of steps runs on
+    // a stream of its own, forked from and joined back into the caller's
+    cudaStream_t vstream[kNumVariants] = {};
+    cudaEvent_t fork_ev = nullptr;
+    cudaEvent_t join_ev[kNumVariants] = {};
+    int nvariants = 0;  // non-empty variants
     std::map<int, cudaGraphExec_t> graphs;  // by nsteps
     std::map<int, cudaGraph_t> graph_defs;
 };
@@ -191,20 +199,38 @@ int enqueue_steps(mpdata_batch *b, int nsteps, cudaStream_t s) {
             if (e != cudaSuccess) return bcuda(e, "cudaMemcpyAsync");
         }
     }
-    for (int st = 0; st < nsteps; ++st) {
-        const int parity = (nsteps & 1) ? ((st + 1) & 1) : (st & 1);
-        for (int v = 0; v < kNumVariants; ++v) {
-            Group &G = b->group[v];
-            if (G.items.empty()) continue;
-            const int nonosc = b->opts.nonoscillatory, lid = variant_lid(v);
+    // The grids of different variants are disjoint, so with several variants
+    // each one's steps run on its own stream: the launches of one variant
+    // fill the SMs that another's last wave of tiles leaves idle.
+    const bool fork = b->nvariants > 1;
+    if (fork) {
+        cudaError_t e = cudaEventRecord(b->fork_ev, s);
+        if (e != cudaSuccess) return bcuda(e, "cudaEventRecord");
+    }
+    for (int v = 0; v < kNumVariants; ++v) {
+        Group &G = b->group[v];
+        if (G.items.empty()) continue;
+        cudaStream_t vs = fork ? b->vstream[v] : s;
+        if (fork) {
+            cudaError_t e = cudaStreamWaitEvent(vs, b->fork_ev, 0);
+            if (e != cudaSuccess) return bcuda(e, "cudaStreamWaitEvent");
+        }
+        const int nonosc = b->opts.nonoscillatory, lid = variant_lid(v);
+        const int ty = variant_tile_y(v), ld = variant_ld(v);
+        for (int st = 0; st < nsteps; ++st) {
+            const int parity = (nsteps & 1) ? ((st + 1) & 1) : (st & 1);
             cudaError_t e;
-            const int ty = variant_tile_y(v), ld = variant_ld(v);
             if (direct[v])
-                e = mpdata::launch_fused_pairs_direct(ty, ld, nonosc, lid, *direct[v], parity, s);
+                e = mpdata::launch_fused_pairs_direct(ty, ld, nonosc, lid, *direct[v], parity, vs);
             else
                 e = mpdata::launch_fused_pairs_batch(32, ty, ld, nonosc, lid, b->d_grids, G.d_items,
-                                                     G.d_begin, G.ncta, parity, s);
+                                                     G.d_begin, G.ncta, parity, vs);
             if (e != cudaSuccess) return bcuda(e, "batched kernel launch");
+        }
+        if (fork) {
+            cudaError_t e = cudaEventRecord(b->join_ev[v], vs);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(s, b->join_ev[v], 0);
+            if (e != cudaSuccess) return bcuda(e, "joining a variant's stream");
         }
     }
     return MPDATA_OK;
@@ -299,6 +325,16 @@ int mpdata_batch_create_tiles(int ngrids, const int *dims, const int *periodic, 
     }
     e = cudaMalloc((void **)&b->d_grids, sizeof(BatchGrid) * ngrids);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->capture_stream, cudaStreamNonBlocking);
+    for (int v = 0; v < kNumVariants; ++v)
+        if (!b->group[v].items.empty()) ++b->nvariants;
+    if (b->nvariants > 1) {
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork_ev, cudaEventDisableTiming);
+        for (int v = 0; v < kNumVariants && e == cudaSuccess; ++v) {
+            if (b->group[v].items.empty()) continue;
+            e = cudaStreamCreateWithFlags(&b->vstream[v], cudaStreamNonBlocking);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->join_ev[v], cudaEventDisableTiming);
+        }
+    }
     if (e != cudaSuccess) { mpdata_batch_destroy(b); return bcuda(e, "batch allocation"); }
     *out = b;
     return MPDATA_OK;
@@ -414,6 +450,11 @@ int mpdata_batch_destroy(mpdata_batch_t *b) {
     for (auto &G : b->group) { cudaFree(G.d_items); cudaFree(G.d_begin); }
     cudaFree(b->d_grids);
     if (b->capture_stream) cudaStreamDestroy(b->capture_stream);
+    for (int v = 0; v < kNumVariants; ++v) {
+        if (b->vstream[v]) cudaStreamDestroy(b->vstream[v]);
+        if (b->join_ev[v]) cudaEventDestroy(b->join_ev[v]);
+    }
+    if (b->fork_ev) cudaEventDestroy(b->fork_ev);
     delete b;
     return MPDATA_OK;
 }
