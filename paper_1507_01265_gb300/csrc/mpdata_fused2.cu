@@ -719,8 +719,8 @@ __global__ void __launch_bounds__(LD ? Lay2<TX, TY>::NTW + Lay2<TX, TY>::NLD : L
     pairs_tile<TX, TY, NONOSC, LID, LD ? 1 : 2, LD>(batch_args(d.g[r], parity), d.tile0[r] + c - d.start[r], sm);
 }
 
-// Loader warps serve the 24- and 28-row tiles of launches whose grids all have
-// nx % 4 == 0 (16-byte loads); 16-row tiles and any other nx keep the
+// Loader warps serve the 12-, 24- and 28-row tiles of launches whose grids all
+// have nx % 4 == 0 (16-byte loads); 16-row tiles and any other nx keep the
 // compute threads' own loads.
 template <int TY>
 constexpr bool has_loaders() { return TY == 12 || TY == 24 || TY == 28; }
