@@ -131,7 +131,8 @@ def measured_peaks():
 
 
 # the fused FP32 kernels and the tile / row-band planner that picks them
-FUSED_SOURCES = ("mpdata_fused2.cu", "mpdata_internal.cuh", "mpdata_fused.cu")
+FUSED_SOURCES = ("mpdata_fused2.cuh", "mpdata_fused2.cu", "mpdata_fused2_t12.cu", "mpdata_fused2_t16.cu",
+                 "mpdata_fused2_t24.cu", "mpdata_fused2_t28.cu", "mpdata_internal.cuh", "mpdata_fused.cu")
 
 
 def _code_only(text):
