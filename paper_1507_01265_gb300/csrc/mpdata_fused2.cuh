@@ -241,7 +241,7 @@ using BT = std::integral_constant<bool, true>;
 using BF = std::integral_constant<bool, false>;
 
 // Loader warps of the two-column tile (k_fused_pairs with LD): threads NTW ..
-// NTW + 63 issue every 16-byte input load of the tile and wait for them, on
+// NTW + NLD - 1 issue every 16-byte input load of the tile and wait for them, on
 // the same schedule and with the same barriers (three per plane and one at the
 // end) as pairs_tile, so that the compute threads carry no load state.
 template <int TX, int TY, bool LID>
